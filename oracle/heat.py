@@ -1,0 +1,113 @@
+"""Poisson solve, BDF1 heat stepping and its discrete adjoint (oracle; test infrastructure only).
+
+All arrays are half-complex coefficient arrays [p][m][n] (see ``transforms``).
+Each half-complex slice is a real slice of one wavenumber |k|; the operators
+are real and depend on k^2 only (eq. HelmholtzMatEqn), so every slice is an
+independent real matrix equation ("decouple in theta", Section 3).
+
+* ``poisson``     -- -lap u = f with zero Dirichlet data (Section 4 Poisson
+                     solves; Section 3 machinery without the identity term).
+* ``heat_steps``  -- BDF1 (Section 3, BDF 1: kappa = h, delta X = X_n) with the
+                     forcing of step n -> n+1 taken at level n (the
+                     extrapolation g(t+h) ~ g(t) stated beside eq.
+                     HelmholtzMatEqn).
+* ``heat_adjoint``-- gradients of a scalar loss of X_N with respect to X_0,
+                     every g_n and alpha, by the chain rule through the
+                     direct solves (no part of the paper; the transpose of
+                     the stepping map above).
+"""
+import numpy as np
+
+from .sylvester import ModeSystem, BartelsStewart, solve_kron
+from .transforms import slice_wavenumber
+
+
+def _systems(m, n, p, kind, kappa_alpha=None):
+    """One ModeSystem and direct solver per distinct |k| (slices share them)."""
+    out = {}
+    for s in range(p):
+        k = slice_wavenumber(s, p)
+        if k not in out:
+            ms = ModeSystem(m, n, k, kind, kappa_alpha)
+            out[k] = (ms, BartelsStewart(ms.A, ms.B, ms.C, ms.D))
+    return out
+
+
+def poisson(F, slices=None, brute=False):
+    """Coefficients u of -lap u = f for half-complex coefficients F of f."""
+    p, m, n = F.shape
+    sys_ = _systems(m, n, p, 'poisson')
+    U = np.zeros_like(F)
+    for s in (range(p) if slices is None else slices):
+        ms, bs = sys_[slice_wavenumber(s, p)]
+        E = ms.rhs(F[s])
+        Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+        U[s] = ms.expand(Y)
+    return U
+
+
+def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=False):
+    """BDF1: X_{n+1} solves eq. HelmholtzMatEqn with delta X = X_n, kappa = dt.
+
+    g is either one coefficient array (constant forcing) or an array of
+    shape [nsteps][p][m][n] (g[n] is used by the step n -> n+1)."""
+    p, m, n = X0.shape
+    kappa = dt
+    sys_ = _systems(m, n, p, 'heat', kappa * alpha)
+    g = np.asarray(g, dtype=np.float64)
+    X = np.array(X0, dtype=np.float64, copy=True)
+    traj = [X.copy()] if return_all else None
+    todo = range(p) if slices is None else slices
+    for step in range(nsteps):
+        gn = g[step] if g.ndim == 4 else g
+        Xn = np.zeros_like(X)
+        for s in todo:
+            ms, bs = sys_[slice_wavenumber(s, p)]
+            E = ms.rhs(X[s] + kappa * gn[s])
+            Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+            Xn[s] = ms.expand(Y)
+        X = Xn
+        if return_all:
+            traj.append(X.copy())
+    return (X, traj) if return_all else X
+
+
+def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN):
+    """Reverse-mode derivatives of L(X_N) for the BDF1 stepping above.
+
+    Returns (dL/dX0, dL/dg, dL/dalpha); dL/dg has the shape of g (summed over
+    the steps when g is one constant array).
+
+    Step map per slice: E = Rhs(X_n + kappa g_n), Y = Sylv^-1 E, X_{n+1} = S Y S^T,
+    with Sylv(Y) = A Y B^T + C Y D^T, A = C - kappa alpha Lr, D = -kappa alpha D2z.
+    Reverse: mu = S^T lam S; Lam = Sylv^-T mu; lam_n = Rhs^T Lam;
+    dL/dg_n = kappa lam_n; dL/dalpha += -<Lam, dSylv/dalpha Y_{n+1}>,
+    dSylv/dalpha Y = kappa (dA Y B^T + C Y dD^T)."""
+    p, m, n = X0.shape
+    kappa = dt
+    sys_ = _systems(m, n, p, 'heat', kappa * alpha)
+    g = np.asarray(g, dtype=np.float64)
+    const_g = g.ndim == 3
+    _, traj = heat_steps(X0, g, alpha, dt, nsteps, return_all=True)
+    lam = np.array(dL_dXN, dtype=np.float64, copy=True)
+    dg = np.zeros_like(g)
+    dalpha = 0.0
+    for step in reversed(range(nsteps)):
+        Xnext = traj[step + 1]
+        lam_prev = np.zeros_like(lam)
+        for s in range(p):
+            ms, bs = sys_[slice_wavenumber(s, p)]
+            mu = ms.expand_T(lam[s])
+            Lam = bs.solve_T(mu)
+            w = ms.rhs_T(Lam)
+            lam_prev[s] = w
+            if const_g:
+                dg[s] += kappa * w
+            else:
+                dg[step, s] = kappa * w
+            Y = np.linalg.lstsq(ms.Sr, np.linalg.lstsq(ms.Sz, Xnext[s].T, rcond=None)[0].T,
+                                rcond=None)[0]
+            dS = kappa * (ms.dA @ Y @ ms.B.T + ms.C @ Y @ ms.dD.T)
+            dalpha -= float(np.sum(Lam * dS))
+        lam = lam_prev
+    return lam, dg, dalpha
