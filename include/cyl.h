@@ -1,0 +1,196 @@
+/*
+ * cyl.h -- C ABI of libcyl, a GB300-native (sm_103a) FP64 implementation of the
+ * Chebyshev-Chebyshev-Fourier (CCF) solver for the heat and Poisson equations in
+ * the closed cylinder r <= 1, z in [-1, 1] (Darrow, arXiv 2206.04827).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid sizes follow Section 2: m = n_r radial, n = n_z vertical, p = n_theta
+ * angular points of the doubled grid (Definition "grid"); N = m n p unknowns.
+ *
+ * Array layout (values and coefficients alike): row-major [p][m][n] float64,
+ * i.e. index (l, j, k) at offset (l * m + j) * n + k, z fastest.
+ *   * Values are samples on the doubled grid of Definition "grid".
+ *   * Coefficients are those of the unique CCF interpolant (Section 2,
+ *     interpolant f*), stored half-complex along theta: slice 0 holds c_0,
+ *     slices 2w-1 and 2w hold Re c_w and Im c_w (w = 1 .. p/2-1), slice p-1
+ *     holds the (real) Nyquist coefficient c_{-p/2}.  Negative wavenumbers are
+ *     implied by c_{-w} = conj(c_w); only real fields are represented.
+ *
+ * Boundary data: homogeneous Dirichlet at r = +-1 (the doubled radius: r = -1
+ * is the physical wall at theta + pi) and z = +-1.  The paper does not state
+ * its boundary conditions; this is the reading the library implements.
+ *
+ * Radial parity: a real field on the doubled grid has c_{j,k,w} = 0 unless
+ * j = w (mod 2), and every operator couples only equal parities.  By default
+ * the solvers compute the physical parity block and write zeros in the other;
+ * CYL_BOTH_PARITIES solves both blocks (inputs that are not real fields).
+ *
+ * Pointers: unless stated otherwise every array argument is a caller-owned
+ * DEVICE pointer to float64 of N elements, valid on the plan's device.  The
+ * plan owns its operator tables, ADI factors and scratch.  Calls that take
+ * device pointers are asynchronous on the plan's CUDA stream and make no host
+ * synchronisation and no allocation.
+ *
+ * Errors: every entry point returns a cyl_status; no C++ exception crosses the
+ * ABI.  On error the contents of output arrays are unspecified.
+ */
+#ifndef CYL_H
+#define CYL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cyl_plan_s *cyl_plan_t;
+
+typedef enum {
+  CYL_OK = 0,
+  CYL_EINVAL = 1,   /* invalid size, parameter, flag or NULL pointer          */
+  CYL_ENOMEM = 2,   /* host or device allocation failed                       */
+  CYL_ECUDA = 3,    /* a CUDA runtime call failed                             */
+  CYL_ETIMEOUT = 4, /* a bounded device-side wait ran out                      */
+  CYL_ESTATE = 5    /* the plan was not built for this operation              */
+} cyl_status;
+
+/* plan flags */
+#define CYL_WITH_POISSON   1u  /* build the Poisson factors                     */
+#define CYL_WITH_HEAT      2u  /* build the BDF1 heat factors (needs alpha, dt) */
+#define CYL_BOTH_PARITIES  4u  /* solve both radial parity blocks                */
+#define CYL_HOST_ONLY      8u  /* host tables only: no device memory, no kernels */
+#define CYL_FORCE_GLOBAL  16u  /* keep ADI work arrays in global memory          */
+
+/* space selector of cyl_poisson */
+#define CYL_VALUES 0
+#define CYL_COEFFS 1
+
+/*
+ * cyl_plan -- build a solver plan for one grid.
+ *
+ * Section 3: the per-mode matrix equation (eq. HelmholtzMatEqn) and its
+ * Poisson analogue; Algorithm 1 (ADI); the shift choice below Algorithm 1
+ * (Zolotarev-type shifts from K(k), dn and a Moebius map).
+ *
+ *   n_r, n_z   >= 4;  n_theta even and >= 2 (the doubled grid needs theta + pi).
+ *   alpha, dt  > 0 when CYL_WITH_HEAT is set (diffusivity; BDF1 step kappa = dt).
+ *   adi_tol    in (0, 1e-2]: target relative accuracy of the Zolotarev bound;
+ *              the iteration count per mode is J = ceil(log(16 gamma) log(4/tol) / pi^2).
+ *   flags      CYL_WITH_POISSON and/or CYL_WITH_HEAT, optionally
+ *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL.
+ *   stream     cudaStream_t on which every device call of this plan runs
+ *              (NULL = legacy default stream).  Ignored with CYL_HOST_ONLY.
+ *
+ * Builds the banded operators from the three-term relations, estimates the
+ * spectral intervals of both pencils per wavenumber, computes the shifts,
+ * factors every shifted banded matrix (LU without pivoting, reciprocal
+ * pivots) and uploads everything.  Allocates host and device memory; not
+ * for use inside stream capture.  *plan is set to NULL on error.
+ */
+cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alpha,
+                    double dt, double adi_tol, unsigned flags, void *stream);
+
+/* Release a plan and all memory it owns (NULL is accepted). */
+cyl_status cyl_destroy(cyl_plan_t plan);
+
+/*
+ * cyl_vals2coeffs -- Section 2, the DCT-I in r, DCT-I in z and DFT in theta
+ * that take grid values to interpolation coefficients.  vals and coeffs are
+ * device arrays of N float64 ([p][m][n]); they may alias.
+ */
+cyl_status cyl_vals2coeffs(cyl_plan_t plan, const double *vals, double *coeffs);
+
+/* cyl_coeffs2vals -- inverse of cyl_vals2coeffs (evaluation of f* on the grid). */
+cyl_status cyl_coeffs2vals(cyl_plan_t plan, const double *coeffs, double *vals);
+
+/*
+ * cyl_poisson -- solve -lap u = f, zero Dirichlet data (the Poisson solves of
+ * Section 4, with the Section 3 discretisation without its identity term).
+ * f and u are device arrays of N float64; space = CYL_VALUES (both are grid
+ * values) or CYL_COEFFS (both are half-complex coefficients).  f and u may
+ * alias.  Needs CYL_WITH_POISSON.
+ */
+cyl_status cyl_poisson(cyl_plan_t plan, const double *f, double *u, int space);
+
+/*
+ * cyl_heat_step -- advance (d_t - alpha lap) T = g by nsteps BDF1 steps
+ * (Section 3, BDF 1 and eq. HelmholtzMatEqn with kappa = dt, delta X = X_n;
+ * the forcing of step n -> n+1 is g at level n).
+ *
+ *   T              device, N float64 coefficients; in: T_0, out: T_nsteps.
+ *   g              device coefficients, or NULL for g = 0.
+ *   g_step_stride  0: the same g every step; otherwise step n reads
+ *                  g + n * g_step_stride (elements, >= N).
+ *   ckpt           NULL, or device array of (nsteps / ckpt_every + 1) * N
+ *                  float64 that receives T_0, T_c, T_2c, ... (c = ckpt_every).
+ *   ckpt_every     >= 1 when ckpt is given.
+ * Needs CYL_WITH_HEAT.
+ */
+cyl_status cyl_heat_step(cyl_plan_t plan, double *T, const double *g, long long g_step_stride,
+                         int nsteps, double *ckpt, int ckpt_every);
+
+/*
+ * cyl_heat_adjoint -- reverse-mode derivatives of a scalar loss L(T_N) of the
+ * BDF1 run that cyl_heat_step(T0, g, g_step_stride, nsteps) computes.  Not in
+ * the paper: the exact transpose of that linear stepping map, i.e. the
+ * transposed Sylvester solves run backward through the steps, with the states
+ * recomputed from checkpoints every ckpt_every steps.
+ *
+ *   T0, g, g_step_stride, nsteps   as for cyl_heat_step (T0 is not modified).
+ *   dL_dTN      device, N float64: dL/dT_N (coefficient layout).
+ *   dL_dT0      device, N float64 output.
+ *   dL_dg       NULL, or device output shaped like g: N float64 when
+ *               g_step_stride = 0 (summed over steps), else nsteps arrays at
+ *               stride g_step_stride.
+ *   dL_dalpha   NULL, or device pointer to ONE float64 output.
+ *   ckpt_every  >= 1; states are recomputed in segments of this length.
+ * Needs CYL_WITH_HEAT.
+ */
+cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
+                            long long g_step_stride, int nsteps, int ckpt_every,
+                            const double *dL_dTN, double *dL_dT0, double *dL_dg,
+                            double *dL_dalpha);
+
+/* Human-readable name of a status code (static string). */
+const char *cyl_status_string(cyl_status s);
+
+/* ---------------------------------------------------------------------------
+ * Host-side introspection (no device access; valid on CYL_HOST_ONLY plans).
+ * ------------------------------------------------------------------------- */
+
+/* which: 0 = Poisson, 1 = heat.  k = |wavenumber| in 0 .. n_theta/2;
+ * parity = radial parity block (0 or 1).
+ * Returns J and, when the pointers are non-NULL, the spectral interval
+ * [a, b] of the radial pencil, [c, d] of the vertical pencil (Section 3, the
+ * intervals below Algorithm 1) and the J shift pairs: p_shift[j] (used in
+ * the radial solve, lies in [c, d]) and q_shift[j] (used in the vertical
+ * solve, lies in [a, b]).  p_shift / q_shift must hold J doubles; call once
+ * with NULL to learn J. */
+cyl_status cyl_plan_shifts(cyl_plan_t plan, int which, int k, int parity, int *J,
+                           double *interval4, double *p_shift, double *q_shift);
+
+/* Copy the parity block (class index rows/cols) of one plan operator to a
+ * dense row-major host array.  op: 0 = A (radial, per k), 1 = C (radial),
+ * 2 = B (vertical), 3 = D (vertical); which as above; parity selects the
+ * radial (op 0, 1) or vertical (op 2, 3) parity class.  *dim receives the
+ * block size; out (dim*dim doubles) may be NULL to query the size. */
+cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int parity, int *dim,
+                             double *out);
+
+/* Grid of Definition "grid" (Section 2) into caller-owned HOST arrays:
+ * r[m] = cos((m-1-j) pi / (m-1)), z[n] likewise, theta[p] = (2l - p) pi / p.
+ * Any pointer may be NULL. */
+cyl_status cyl_grid(cyl_plan_t plan, double *r, double *z, double *theta);
+
+/* Complete elliptic integral K as a function of the complementary modulus
+ * k' (so that k = sqrt(1 - k'^2) never loses precision), and the Jacobi
+ * function dn(u | k) with the same argument convention (DLMF 19.8, 22.20). */
+double cyl_ellip_K(double kprime);
+double cyl_jacobi_dn(double u, double kprime);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CYL_H */

@@ -22,15 +22,19 @@ from .sylvester import ModeSystem, BartelsStewart, solve_kron
 from .transforms import slice_wavenumber
 
 
-def _systems(m, n, p, kind, kappa_alpha=None):
-    """One ModeSystem and direct solver per distinct |k| (slices share them)."""
-    out = {}
-    for s in range(p):
-        k = slice_wavenumber(s, p)
-        if k not in out:
-            ms = ModeSystem(m, n, k, kind, kappa_alpha)
-            out[k] = (ms, BartelsStewart(ms.A, ms.B, ms.C, ms.D))
-    return out
+class _systems(dict):
+    """One ModeSystem and direct solver per distinct |k| (slices share them),
+    built on first use."""
+
+    def __init__(self, m, n, p, kind, kappa_alpha=None):
+        super().__init__()
+        self.args = (m, n, kind, kappa_alpha)
+
+    def __missing__(self, k):
+        m, n, kind, ka = self.args
+        ms = ModeSystem(m, n, k, kind, ka)
+        self[k] = (ms, BartelsStewart(ms.A, ms.B, ms.C, ms.D))
+        return self[k]
 
 
 def poisson(F, slices=None, brute=False):

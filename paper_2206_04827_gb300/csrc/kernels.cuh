@@ -1,0 +1,42 @@
+// Launch wrappers of the libcyl device kernels (internal header).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace cyl {
+
+// Arguments of one fused ADI launch (one CTA per Item, every step of the run).
+struct AdiArgs {
+  const Item *items;       // device item table
+  int nitems;
+  const double *fac;       // device factor / band tables
+  const double *Xin;       // T-basis coefficients read by the first step ([p][m][n])
+  double *Xout;            // T-basis coefficients written by every step
+  const double *G;         // forcing coefficients (heat) or NULL
+  double kappa;            // F = R_2 (X + kappa g) C02^T
+  long long gstride;       // per-step stride of G (0 = constant)
+  int nsteps;
+  double *ckpt;            // NULL or checkpoint slots of N doubles
+  int ckpt_every;
+  int m, n, p;
+  int zero_other;          // write zeros into the non-solved radial parity rows
+  int transpose;           // 0: forward solve, 1: transposed (adjoint) solve
+  double *gwork;           // global work arrays when the item does not fit in shared memory
+  long long gwork_per_item;
+  int use_smem;
+  int ld;                  // leading dimension of the work arrays (odd)
+  int smem_rows;           // rows of the S array (max Mfull)
+  int maxM, maxNz;         // band table sizes in shared memory
+};
+
+size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem);
+
+cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st);
+
+// out[o][j][i] = sum_t W[j][t] in[o][t][i]  (dense transform along one axis)
+cudaError_t launch_axis_matvec(const double *in, double *out, const double *W, long long outer, int L,
+                               long long inner, cudaStream_t st);
+
+}  // namespace cyl

@@ -1,0 +1,104 @@
+// Internal plan representation of libcyl (host side).  Not part of the ABI.
+//
+// Notation (Section 3): per wavenumber k the BDF step / Poisson problem is the
+// generalised Sylvester equation  A Y B^T + C Y D^T = E  on the Dirichlet
+// recombined coefficients Y (X = S_r Y S_z^T, phi_j = T_{j+2} - T_j).  Every
+// operator has even bandwidth offsets, so the equation splits into parity
+// blocks ("class" indices a = (i - parity) / 2).  Block bands:
+//   radial  A, C : offsets -2 .. +3        vertical  B : -1 .. +2,  D : 0 .. +1
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace cyl {
+
+// Square banded matrix: entry (i, j) stored when j - i lies in [-lo, hi].
+struct Band {
+  int n = 0, lo = 0, hi = 0;
+  std::vector<double> v;
+  Band() = default;
+  Band(int n_, int lo_, int hi_) : n(n_), lo(lo_), hi(hi_), v((size_t)n_ * (lo_ + hi_ + 1), 0.0) {}
+  int w() const { return lo + hi + 1; }
+  bool in(int i, int j) const { return i >= 0 && j >= 0 && i < n && j < n && j - i >= -lo && j - i <= hi; }
+  double get(int i, int j) const { return in(i, j) ? v[(size_t)i * w() + (j - i + lo)] : 0.0; }
+  double &at(int i, int j) { return v[(size_t)i * w() + (j - i + lo)]; }
+};
+
+// Factors per row of one shifted radial matrix (A - p C) for iteration j,
+// pre-scaled so that one sweep computes Z = (A - pC)^-1 [(q-p) E + (A - qC) U]:
+//   [0..5]  (A - qC)[i][i+o] / (q-p),  o = -2 .. 3
+//   [6..7]  -L[i][i-1], -L[i][i-2]               (unit lower factor)
+//   [8..10] -U[i][i+o] / (q-p),  o = 1 .. 3       (upper factor)
+//   [11]    (q-p) / U[i][i]
+constexpr int RSTRIDE = 12;
+// Factors per column of one vertical matrix (D + qB) and the next apply band:
+//   [0]     -L[c][c-1]
+//   [1..2]  -U[c][c+1], -U[c][c+2]
+//   [3]     1 / U[c][c]
+//   [4..7]  (D + p' B)[c][c+o], o = -1 .. 2      (p' = next radial shift)
+constexpr int ZSTRIDE = 8;
+// Right-hand-side bands: R_2[i][i+2s] (s = -1..3) per radial class row and
+// C02[j][j+2t] (t = 0..2) per vertical class column.
+constexpr int R2STRIDE = 5;
+constexpr int C02STRIDE = 3;
+
+// One unit of ADI work: one or two half-complex slices (Re/Im of the same
+// wavenumber share every operator) x one radial class x one vertical class.
+struct Item {
+  int s0, nsl;        // first slice, number of slices (1 or 2; slice s0+1 when 2)
+  int k, pr, pz;      // |wavenumber|, radial and vertical parity class
+  int M, Mfull;       // unknown rows (class rows < m-2), class rows < m
+  int Nz, Nzfull;     // unknown cols (class cols < n-2), class cols < n
+  int J;              // ADI iterations
+  int pad0;
+  long long roff;     // offset (doubles) of the radial factors  [J][M][RSTRIDE]
+  long long zoff;     // offset (doubles) of the vertical factors [J][Nz][ZSTRIDE]
+  long long r2off;    // offset of the R_2 band table   [M][R2STRIDE]
+  long long c02off;   // offset of the C02 band table   [Nz][C02STRIDE]
+};
+
+struct Shifts {
+  int J = 0;
+  double a = 0, b = 0, c = 0, d = 0;
+  std::vector<double> p, q;   // p in [c,d] (radial solve), q in [a,b] (vertical solve)
+};
+
+struct KindTables {             // one per problem kind (Poisson / heat)
+  bool built = false;
+  // per (k, pr): shifts; index k * 2 + pr
+  std::vector<Shifts> shifts;
+  std::vector<Item> items;
+  int Jmax = 0;
+};
+
+struct HostPlan {
+  int m = 0, n = 0, p = 0;
+  double alpha = 0, dt = 0, tol = 0;
+  unsigned flags = 0;
+  // radial class sizes and vertical class sizes
+  int Mc[2] = {0, 0}, Mfull[2] = {0, 0}, Nc[2] = {0, 0}, Nfull[2] = {0, 0};
+  // spectra of the unscaled pencils: mu (radial, per k, parity) and nu (vertical, per parity)
+  std::vector<double> mu_min, mu_max;   // index k * 2 + pr
+  double nu_min[2] = {0, 0}, nu_max[2] = {0, 0};
+  KindTables kind[2];                   // 0 = Poisson, 1 = heat
+  std::vector<double> factors;          // all radial and vertical factor rows + rhs bands
+  // transform matrices (row-major, out index major): forward and inverse
+  std::vector<double> Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i;
+
+  // radial block operators per k (lazily usable by introspection)
+  Band Cblk(int pr) const;
+  Band Lblk(int k, int pr) const;
+  Band Bblk(int pz) const;
+  Band D2blk(int pz) const;
+};
+
+// Build everything on the host.  Returns an empty string on success, else a message.
+std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
+                            unsigned flags);
+
+double ellip_K(double kprime);
+double jacobi_dn(double u, double kprime);
+
+}  // namespace cyl

@@ -1,0 +1,181 @@
+"""ctypes binding of libcyl (argument marshalling only: every step of the
+solver runs in the library's CUDA kernels).
+
+Importing this module loads ``libcyl.so`` from the package directory and
+raises ImportError when it has not been built (``python -m
+paper_2206_04827_gb300.build``); there is no fallback implementation.
+
+Device arrays are passed as torch CUDA tensors (float64, contiguous, layout
+[p][m][n]); torch supplies the memory and the stream, nothing else.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, 'libcyl.so')
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError('libcyl.so is not built (run python -m paper_2206_04827_gb300.build)')
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes and flags (include/cyl.h)
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
+WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL = 1, 2, 4, 8, 16
+VALUES, COEFFS = 0, 1
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_sig = {
+    'cyl_plan': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_uint, _vp]),
+    'cyl_destroy': (ctypes.c_int, [_vp]),
+    'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
+    'cyl_coeffs2vals': (ctypes.c_int, [_vp, _vp, _vp]),
+    'cyl_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    'cyl_heat_step': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int]),
+    'cyl_heat_adjoint': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                        _vp, _vp]),
+    'cyl_status_string': (ctypes.c_char_p, [ctypes.c_int]),
+    'cyl_plan_shifts': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       _c_double_p, _c_double_p, _c_double_p]),
+    'cyl_plan_operator': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), _c_double_p]),
+    'cyl_grid': (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
+    'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
+    'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class CylError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__('%s: %s' % (what, _lib.cyl_status_string(status).decode()))
+        self.status = status
+
+
+def _check(status, what):
+    if status != OK:
+        raise CylError(status, what)
+
+
+def status_string(s):
+    return _lib.cyl_status_string(s).decode()
+
+
+def ellip_K(kprime):
+    return _lib.cyl_ellip_K(kprime)
+
+
+def jacobi_dn(u, kprime):
+    return _lib.cyl_jacobi_dn(u, kprime)
+
+
+def _ptr(t, name, numel=None):
+    """Device pointer of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError('%s must be a contiguous float64 CUDA tensor' % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError('%s holds %d elements, needs %d' % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owner of one ``cyl_plan_t`` (see include/cyl.h: cyl_plan)."""
+
+    def __init__(self, n_r, n_z, n_theta, alpha=0.0, dt=0.0, adi_tol=1e-14, poisson=True, heat=False,
+                 both_parities=False, host_only=False, force_global=False, stream=None):
+        flags = (WITH_POISSON if poisson else 0) | (WITH_HEAT if heat else 0) \
+            | (BOTH_PARITIES if both_parities else 0) | (HOST_ONLY if host_only else 0) \
+            | (FORCE_GLOBAL if force_global else 0)
+        if stream is None and not host_only:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = _vp()
+        _check(_lib.cyl_plan(ctypes.byref(self._h), int(n_r), int(n_z), int(n_theta), float(alpha), float(dt),
+                             float(adi_tol), flags, _vp(stream) if stream else None), 'cyl_plan')
+        self.m, self.n, self.p = int(n_r), int(n_z), int(n_theta)
+        self.N = self.m * self.n * self.p
+        self.alpha, self.dt = float(alpha), float(dt)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.cyl_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- device calls -------------------------------------------------------
+    def vals2coeffs(self, vals, coeffs):
+        _check(_lib.cyl_vals2coeffs(self._h, _ptr(vals, 'vals', self.N), _ptr(coeffs, 'coeffs', self.N)),
+               'cyl_vals2coeffs')
+        return coeffs
+
+    def coeffs2vals(self, coeffs, vals):
+        _check(_lib.cyl_coeffs2vals(self._h, _ptr(coeffs, 'coeffs', self.N), _ptr(vals, 'vals', self.N)),
+               'cyl_coeffs2vals')
+        return vals
+
+    def poisson(self, f, u, space=COEFFS):
+        _check(_lib.cyl_poisson(self._h, _ptr(f, 'f', self.N), _ptr(u, 'u', self.N), int(space)), 'cyl_poisson')
+        return u
+
+    def heat_step(self, T, g=None, nsteps=1, g_step_stride=0, ckpt=None, ckpt_every=1):
+        need = None if ckpt is None else (nsteps // ckpt_every + 1) * self.N
+        _check(_lib.cyl_heat_step(self._h, _ptr(T, 'T', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
+                                  int(nsteps), _ptr(ckpt, 'ckpt', need), int(ckpt_every)), 'cyl_heat_step')
+        return T
+
+    def heat_adjoint(self, T0, g, nsteps, dL_dTN, dL_dT0, dL_dg=None, dL_dalpha=None, g_step_stride=0,
+                     ckpt_every=1):
+        _check(_lib.cyl_heat_adjoint(self._h, _ptr(T0, 'T0', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
+                                     int(nsteps), int(ckpt_every), _ptr(dL_dTN, 'dL_dTN', self.N),
+                                     _ptr(dL_dT0, 'dL_dT0', self.N), _ptr(dL_dg, 'dL_dg', self.N),
+                                     _ptr(dL_dalpha, 'dL_dalpha', 1)), 'cyl_heat_adjoint')
+        return dL_dT0
+
+    # -- host introspection ---------------------------------------------------
+    def grid(self):
+        """(r, z, theta) of the doubled grid (host arrays)."""
+        r = (ctypes.c_double * self.m)()
+        z = (ctypes.c_double * self.n)()
+        t = (ctypes.c_double * self.p)()
+        _check(_lib.cyl_grid(self._h, r, z, t), 'cyl_grid')
+        return np.array(r), np.array(z), np.array(t)
+
+    def shifts(self, which, k, parity):
+        """(J, (a, b, c, d), p_shifts, q_shifts) of one wavenumber (host tables)."""
+        J = ctypes.c_int()
+        _check(_lib.cyl_plan_shifts(self._h, which, k, parity, ctypes.byref(J), None, None, None), 'cyl_plan_shifts')
+        iv = (ctypes.c_double * 4)()
+        ps = (ctypes.c_double * J.value)()
+        qs = (ctypes.c_double * J.value)()
+        _check(_lib.cyl_plan_shifts(self._h, which, k, parity, ctypes.byref(J), iv, ps, qs), 'cyl_plan_shifts')
+        return J.value, tuple(iv), np.array(ps), np.array(qs)
+
+    def operator(self, op, which, k, parity):
+        """Dense parity block of A (op 0), C (1), B (2) or D (3)."""
+        d = ctypes.c_int()
+        _check(_lib.cyl_plan_operator(self._h, op, which, k, parity, ctypes.byref(d), None), 'cyl_plan_operator')
+        buf = (ctypes.c_double * (d.value * d.value))()
+        _check(_lib.cyl_plan_operator(self._h, op, which, k, parity, ctypes.byref(d), buf), 'cyl_plan_operator')
+        return np.array(buf).reshape(d.value, d.value)
+
+
+def exported_symbols():
+    """Names of the functions the binding requires from libcyl."""
+    return sorted(_sig)

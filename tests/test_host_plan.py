@@ -1,0 +1,156 @@
+"""Host-side logic of libcyl, run on the CPU through the C ABI (no device
+calls): exported symbols, elliptic functions, the plan's operator blocks
+against the oracle, spectral intervals, Zolotarev shifts and their ADI
+convergence, and argument validation."""
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import sylvester as sy
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope='module')
+def cyl():
+    from paper_2206_04827_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_2206_04827_gb300 import cyl as C
+    return C
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, 'include', 'cyl.h')).read()
+    txt = re.sub(r'/\*.*?\*/', '', txt, flags=re.S)
+    return sorted(set(re.findall(r'\b(cyl_[A-Za-z0-9_]+)\s*\(', txt)))
+
+
+def test_library_exports_every_declared_function(cyl):
+    names = _header_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(cyl._lib, name), name
+    assert set(cyl.exported_symbols()) <= set(names)
+
+
+@pytest.mark.parametrize('kp', [0.9, 0.5, 1e-2, 1e-4, 1e-6, 1e-9])
+def test_elliptic_functions_match_high_precision(cyl, kp):
+    """K against scipy, K and dn against 40-digit mpmath (scipy's dn loses
+    digits near u = K when k' is small)."""
+    mp = pytest.importorskip('mpmath')
+    mp.mp.dps = 40
+    K = cyl.ellip_K(kp)
+    assert K == pytest.approx(special.ellipkm1(kp * kp), rel=1e-13)
+    m = 1 - mp.mpf(kp) ** 2
+    assert K == pytest.approx(float(mp.ellipk(m)), rel=1e-14)
+    for frac in (0.0, 0.1, 0.37, 0.5, 0.8, 0.97):
+        u = frac * K
+        assert cyl.jacobi_dn(u, kp) == pytest.approx(float(mp.ellipfun('dn', u, m=m)), rel=1e-12)
+
+
+@pytest.mark.parametrize('kp', [1e-5, 1e-8, 4e-9, 1e-12])
+def test_dn_identities_for_tiny_complementary_modulus(cyl, kp):
+    """dn(0) = 1, dn(K) = k', dn(u) dn(K - u) = k' (DLMF 22.5, 22.4)."""
+    K = cyl.ellip_K(kp)
+    assert K == pytest.approx(np.log(4.0 / kp), rel=1e-6)
+    assert cyl.jacobi_dn(0.0, kp) == pytest.approx(1.0, rel=1e-15)
+    assert cyl.jacobi_dn(K, kp) == pytest.approx(kp, rel=1e-10)
+    for frac in (0.05, 0.3, 0.5, 0.71, 0.99):
+        u = frac * K
+        assert cyl.jacobi_dn(u, kp) * cyl.jacobi_dn(K - u, kp) == pytest.approx(kp, rel=1e-10)
+
+
+def _blocks(ms, pr, pz):
+    ir = np.arange(pr, ms.m - 2, 2)
+    iz = np.arange(pz, ms.n - 2, 2)
+    return (ms.A[np.ix_(ir, ir)], ms.C[np.ix_(ir, ir)], ms.B[np.ix_(iz, iz)], ms.D[np.ix_(iz, iz)])
+
+
+@pytest.mark.parametrize('m,n,p', [(9, 8, 6), (12, 13, 8), (33, 20, 4)])
+def test_plan_operators_equal_oracle_blocks(cyl, m, n, p):
+    alpha, dt = 0.7, 0.01
+    plan = cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=True, heat=True, both_parities=True, host_only=True)
+    for which, kind, ka in ((0, 'poisson', None), (1, 'heat', alpha * dt)):
+        for k in range(p // 2 + 1):
+            ms = sy.ModeSystem(m, n, k, kind, ka)
+            for par in (0, 1):
+                A, C, B, D = _blocks(ms, par, par)
+                assert np.allclose(plan.operator(0, which, k, par), A, atol=1e-12 * np.abs(A).max())
+                assert np.allclose(plan.operator(1, which, k, par), C, atol=1e-14)
+                assert np.allclose(plan.operator(2, which, k, par), B, atol=1e-14)
+                assert np.allclose(plan.operator(3, which, k, par), D, atol=1e-12 * max(np.abs(D).max(), 1))
+    plan.close()
+
+
+@pytest.mark.parametrize('m,n,p', [(17, 17, 8), (33, 33, 32), (64, 48, 16)])
+def test_intervals_contain_spectra_and_shifts_lie_inside(cyl, m, n, p):
+    alpha, dt = 1.0, 1e-3
+    plan = cyl.Plan(m, n, p, alpha, dt, 1e-14, poisson=True, heat=True, host_only=True)
+    for which, kind, ka in ((0, 'poisson', None), (1, 'heat', alpha * dt)):
+        for k in sorted({0, 1, 2, p // 4, p // 2}):
+            par = k % 2
+            J, (a, b, c, d), ps, qs = plan.shifts(which, k, par)
+            ms = sy.ModeSystem(m, n, k, kind, ka)
+            for pz in (0, 1):
+                A, C, B, D = _blocks(ms, par, pz)
+                eP = np.linalg.eigvals(np.linalg.solve(C, A))
+                eQ = -np.linalg.eigvals(np.linalg.solve(B, D))
+                assert np.abs(eP.imag).max() < 1e-6 * np.abs(eP).max()
+                assert a <= eP.real.min() and eP.real.max() <= b
+                assert c <= eQ.real.min() and eQ.real.max() <= d
+            assert np.all((qs >= a) & (qs <= b)) and np.all((ps >= c) & (ps <= d))
+            gam = abs(c - a) * abs(d - b) / (abs(c - b) * abs(d - a))
+            assert J == int(np.ceil(np.log(16 * gam) * np.log(4 / 1e-14) / np.pi ** 2))
+    plan.close()
+
+
+def _adi(A, B, C, D, E, ps, qs):
+    """Algorithm 1 with the plan's shifts (host-side convention check)."""
+    U = np.zeros_like(E)
+    for j in range(len(ps)):
+        p_, q_ = ps[j], qs[j]
+        Z = np.linalg.solve(A - p_ * C, (q_ - p_) * E + (A - q_ * C) @ U)
+        X = np.linalg.solve(D + q_ * B, Z.T).T
+        U = X @ (D + (ps[j + 1] if j + 1 < len(ps) else 0.0) * B).T
+    return X
+
+
+@pytest.mark.parametrize('kind', ['poisson', 'heat'])
+def test_plan_shifts_make_adi_converge_to_direct_solve(cyl, kind):
+    m, n, p = 40, 36, 8
+    alpha, dt = 0.5, 2e-3
+    plan = cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=True, heat=True, host_only=True)
+    which = 0 if kind == 'poisson' else 1
+    rng = np.random.default_rng(4)
+    for k in (0, 3, 4):
+        par = k % 2
+        J, _, ps, qs = plan.shifts(which, k, par)
+        for pz in (0, 1):
+            A, C, B, D = (plan.operator(o, which, k, pz if o > 1 else par) for o in range(4))
+            ii, jj = np.meshgrid(np.arange(A.shape[0]), np.arange(B.shape[0]), indexing='ij')
+            E = rng.standard_normal(ii.shape) * 1.3 ** (-(ii + jj))
+            X = _adi(A, B, C, D, E, ps, qs)
+            Xd = sy.solve_kron(A, B, C, D, E)
+            assert np.abs(X - Xd).max() < 1e-12 * np.abs(Xd).max()
+    plan.close()
+
+
+def test_argument_validation(cyl):
+    bad = [dict(n_r=3, n_z=8, n_theta=8), dict(n_r=8, n_z=3, n_theta=8), dict(n_r=8, n_z=8, n_theta=7),
+           dict(n_r=8, n_z=8, n_theta=0), dict(n_r=8, n_z=8, n_theta=8, adi_tol=0.5),
+           dict(n_r=8, n_z=8, n_theta=8, adi_tol=0.0), dict(n_r=8, n_z=8, n_theta=8, heat=True, alpha=-1.0, dt=0.1),
+           dict(n_r=8, n_z=8, n_theta=8, heat=True, alpha=1.0, dt=0.0), dict(n_r=8, n_z=8, n_theta=8, poisson=False)]
+    for kw in bad:
+        kw.setdefault('adi_tol', 1e-12)
+        with pytest.raises(cyl.CylError) as ei:
+            cyl.Plan(host_only=True, **kw)
+        assert ei.value.status == cyl.EINVAL
+    plan = cyl.Plan(8, 8, 8, host_only=True)
+    with pytest.raises(cyl.CylError) as ei:
+        plan.shifts(1, 0, 0)
+    assert ei.value.status == cyl.ESTATE
+    assert cyl.status_string(cyl.ETIMEOUT).startswith('CYL_ETIMEOUT')
