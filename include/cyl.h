@@ -152,6 +152,15 @@ cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
                             const double *dL_dTN, double *dL_dT0, double *dL_dg,
                             double *dL_dalpha);
 
+/*
+ * cyl_sync -- wait for every call queued on the plan's stream, then report
+ * device-side failures of those calls: CYL_ETIMEOUT when a bounded wait inside
+ * a kernel ran out (the affected outputs are then unspecified; the flag is
+ * cleared), CYL_ECUDA for a CUDA error.  Host-synchronising; not for use
+ * inside stream capture.  Not in the paper.
+ */
+cyl_status cyl_sync(cyl_plan_t plan);
+
 /* Human-readable name of a status code (static string). */
 const char *cyl_status_string(cyl_status s);
 

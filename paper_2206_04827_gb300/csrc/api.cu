@@ -31,12 +31,13 @@ struct cyl_plan_s {
   double *d_gwork = nullptr;
   double *d_W[6] = {};          // Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i
   double *d_tmp[3] = {};        // N-element scratch arrays
+  int *d_err = nullptr;         // device status word written by bounded waits
   size_t N = 0;
 };
 
 namespace {
 
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = 227 * 1024 - 1024;   // opt-in limit minus static shared memory
 
 template <class T>
 cudaError_t upload(T **dst, const T *src, size_t count) {
@@ -53,6 +54,7 @@ void free_device(cyl_plan_s *P) {
   cudaFree(P->d_gwork);
   for (auto &p : P->d_W) cudaFree(p);
   for (auto &p : P->d_tmp) cudaFree(p);
+  cudaFree(P->d_err);
 }
 
 cyl_status from_cuda(cudaError_t e) {
@@ -109,6 +111,7 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   a.smem_rows = P->smem_rows;
   a.maxM = P->maxM;
   a.maxNz = P->maxNz;
+  a.err = P->d_err;
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
@@ -195,6 +198,8 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   const std::vector<double> *Ws[6] = {&h.Wr_f, &h.Wr_i, &h.Wz_f, &h.Wz_i, &h.Wt_f, &h.Wt_i};
   for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = upload(&P->d_W[i], Ws[i]->data(), Ws[i]->size());
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc((void **)&P->d_tmp[i], P->N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
   if (e == cudaSuccess && !(P->use_smem[0] && P->use_smem[1])) {
     P->gwork_per_item = ((long long)P->smem_rows * P->ld + (long long)P->maxM * P->ld + 31) / 32 * 32;
     const int maxItems = std::max(P->nitems[0], P->nitems[1]);
@@ -261,6 +266,21 @@ cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, lon
   (void)dL_dg; (void)dL_dalpha;
   if (!P) return CYL_EINVAL;
   return CYL_ESTATE;
+}
+
+cyl_status cyl_sync(cyl_plan_t P) {
+  if (!P) return CYL_EINVAL;
+  if (P->host_only) return CYL_OK;
+  cudaError_t e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) return from_cuda(e);
+  int flag = 0;
+  e = cudaMemcpy(&flag, P->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (flag != 0) {
+    cudaMemset(P->d_err, 0, sizeof(int));
+    return (cyl_status)flag;
+  }
+  return CYL_OK;
 }
 
 cyl_status cyl_grid(cyl_plan_t P, double *r, double *z, double *theta) {

@@ -24,9 +24,44 @@
 namespace cyl {
 
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem) {
-  size_t d = (size_t)maxM * RSTRIDE + (size_t)maxNz * ZSTRIDE;
+  size_t d = 2 * ((size_t)maxM * RSTRIDE + (size_t)maxNz * ZSTRIDE);   // double-buffered factor tables
   if (arrays_in_smem) d += (size_t)smem_rows * ld + (size_t)maxM * ld;
   return d * sizeof(double);
+}
+
+// ------------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// One elected thread: announce `bytes` of transaction and start bulk copies.
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 24); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 // One ADI iteration of Algorithm 1 in the form
@@ -34,109 +69,181 @@ size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in
 //   vertical: X_{j+1} = Z (D + qB)^-T,  U' = X_{j+1} (D + p'B)^T
 // which is the paper's two half-steps (with the signs corrected so that the
 // fixed point solves A X B^T + C X D^T = E) after eliminating the C solve.
+//
+// Every sweep loads the operands of the next row (column) one step ahead
+// into registers: with one warp per SM sub-partition an exposed shared-memory
+// latency idles the FP64 pipe, which is the only resource that matters here.
+template <bool FIRST>
 __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const double *__restrict__ Fc, int ld,
-                                             const double *__restrict__ RB, int M, bool first) {
-  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0, w5;
-  if (!first) {
+                                             const double *__restrict__ RB, int M) {
+  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0;
+  if (!FIRST) {
     if (M > 0) w2 = col[0];
     if (M > 1) w3 = col[ld];
     if (M > 2) w4 = col[2 * ld];
   }
+  double fn = M > 0 ? Fc[0] : 0.0;
+  double un = (!FIRST && M > 3) ? col[3 * ld] : 0.0;
+  const double2 *rb2 = reinterpret_cast<const double2 *>(RB);
+  double2 n01 = rb2[0], n23 = rb2[1], n45 = rb2[2], n67 = rb2[3];
   double y1 = 0.0, y2 = 0.0;
   for (int i = 0; i < M; ++i) {
-    const double *rb = RB + i * RSTRIDE;
-    double acc = Fc[(size_t)i * ld];
-    if (!first) {
-      w5 = (i + 3 < M) ? col[(size_t)(i + 3) * ld] : 0.0;
-      acc = fma(rb[0], w0, acc);
-      acc = fma(rb[1], w1, acc);
-      acc = fma(rb[2], w2, acc);
-      acc = fma(rb[3], w3, acc);
-      acc = fma(rb[4], w4, acc);
-      acc = fma(rb[5], w5, acc);
+    const double f = fn, w5 = un;
+    const double2 a01 = n01, a23 = n23, a45 = n45, a67 = n67;
+    if (i + 1 < M) {
+      fn = Fc[(i + 1) * ld];
+      if (!FIRST) un = (i + 4 < M) ? col[(i + 4) * ld] : 0.0;
+      const double2 *nx = rb2 + (i + 1) * (RSTRIDE / 2);
+      if (!FIRST) { n01 = nx[0]; n23 = nx[1]; n45 = nx[2]; }
+      n67 = nx[3];
+    }
+    double acc = f;
+    if (!FIRST) {
+      acc = fma(a01.x, w0, acc);
+      acc = fma(a01.y, w1, acc);
+      acc = fma(a23.x, w2, acc);
+      acc = fma(a23.y, w3, acc);
+      acc = fma(a45.x, w4, acc);
+      acc = fma(a45.y, w5, acc);
       w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5;
     }
-    acc = fma(rb[6], y1, acc);
-    acc = fma(rb[7], y2, acc);
-    col[(size_t)i * ld] = acc;
+    acc = fma(a67.x, y1, acc);
+    acc = fma(a67.y, y2, acc);
+    col[i * ld] = acc;
     y2 = y1;
     y1 = acc;
   }
   double z1 = 0.0, z2 = 0.0, z3 = 0.0;
+  if (M <= 0) return;
+  double yn = col[(M - 1) * ld];
+  double2 b89 = rb2[(M - 1) * (RSTRIDE / 2) + 4], bab = rb2[(M - 1) * (RSTRIDE / 2) + 5];
   for (int i = M - 1; i >= 0; --i) {
-    const double *rb = RB + i * RSTRIDE;
-    double acc = col[(size_t)i * ld];
-    acc = fma(rb[8], z1, acc);
-    acc = fma(rb[9], z2, acc);
-    acc = fma(rb[10], z3, acc);
-    const double zi = acc * rb[11];
-    col[(size_t)i * ld] = zi;
+    const double y = yn;
+    const double2 c89 = b89, cab = bab;
+    if (i > 0) {
+      yn = col[(i - 1) * ld];
+      b89 = rb2[(i - 1) * (RSTRIDE / 2) + 4];
+      bab = rb2[(i - 1) * (RSTRIDE / 2) + 5];
+    }
+    double acc = fma(c89.x, z1, y);
+    acc = fma(c89.y, z2, acc);
+    acc = fma(cab.x, z3, acc);
+    const double zi = acc * cab.y;
+    col[i * ld] = zi;
     z3 = z2; z2 = z1; z1 = zi;
   }
 }
 
-__device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz,
-                                               bool last) {
+template <bool LAST>
+__device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz) {
+  if (Nz <= 0) return;
   double w = 0.0;
+  double rn = row[0], cn = ZB[0];
   for (int b = 0; b < Nz; ++b) {
-    w = fma(ZB[b * ZSTRIDE + 0], w, row[b]);
+    const double r = rn, c = cn;
+    if (b + 1 < Nz) {
+      rn = row[b + 1];
+      cn = ZB[(b + 1) * ZSTRIDE];
+    }
+    w = fma(c, w, r);
     row[b] = w;
   }
+  const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
   double x1 = 0.0, x2 = 0.0, x3 = 0.0;
+  double2 p01 = z2p[(Nz - 1) * 4], p23 = z2p[(Nz - 1) * 4 + 1], p45, p67;
+  if (!LAST) { p45 = z2p[(Nz - 1) * 4 + 2]; p67 = z2p[(Nz - 1) * 4 + 3]; }
+  double wn = row[Nz - 1];
+  double ap0 = 0.0, ap1 = 0.0, ap2 = 0.0, ap3 = 0.0;   // apply band of column b + 1
   for (int b = Nz - 1; b >= 0; --b) {
-    const double *zb = ZB + b * ZSTRIDE;
-    double v = row[b];
-    v = fma(zb[1], x1, v);
-    v = fma(zb[2], x2, v);
-    const double xb = v * zb[3];
-    if (last) {
+    const double wb = wn;
+    const double2 c01 = p01, c23 = p23;
+    double2 c45, c67;
+    if (!LAST) { c45 = p45; c67 = p67; }
+    if (b > 0) {
+      wn = row[b - 1];
+      p01 = z2p[(b - 1) * 4];
+      p23 = z2p[(b - 1) * 4 + 1];
+      if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
+    }
+    double v = fma(c01.y, x1, wb);
+    v = fma(c23.x, x2, v);
+    const double xb = v * c23.y;
+    if (LAST) {
       row[b] = xb;
-    } else if (b + 1 < Nz) {
-      const double *zn = zb + ZSTRIDE;
-      double u = zn[4] * xb;
-      u = fma(zn[5], x1, u);
-      u = fma(zn[6], x2, u);
-      u = fma(zn[7], x3, u);
-      row[b + 1] = u;
+    } else {
+      if (b + 1 < Nz) {
+        double u = ap0 * xb;
+        u = fma(ap1, x1, u);
+        u = fma(ap2, x2, u);
+        u = fma(ap3, x3, u);
+        row[b + 1] = u;
+      }
+      ap0 = c45.x; ap1 = c45.y; ap2 = c67.x; ap3 = c67.y;
     }
     x3 = x2; x2 = x1; x1 = xb;
   }
-  if (!last && Nz > 0) {
-    double u = ZB[5] * x1;
-    u = fma(ZB[6], x2, u);
-    u = fma(ZB[7], x3, u);
+  if (!LAST) {
+    double u = ap1 * x1;
+    u = fma(ap2, x2, u);
+    u = fma(ap3, x3, u);
     row[0] = u;
   }
 }
 
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
   extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) unsigned long long bar[2];
   const Item it = a.items[blockIdx.x];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz;
   const int ld = a.ld;
   const int m = a.m, n = a.n;
   const long long slice = (long long)m * n;
-  double *RB = sm;
-  double *ZB = RB + (size_t)a.maxM * RSTRIDE;
+  const int rlen = a.maxM * RSTRIDE, zlen = a.maxNz * ZSTRIDE;
+  double *RB0 = sm;                       // [2][maxM * RSTRIDE]
+  double *ZB0 = sm + 2 * rlen;            // [2][maxNz * ZSTRIDE]
   double *S, *Fa;
-  if (a.use_smem) {
-    S = ZB + (size_t)a.maxNz * ZSTRIDE;
+  if (SMEM) {
+    S = ZB0 + 2 * zlen;
   } else {
     S = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
   }
   Fa = S + (size_t)a.smem_rows * ld;
   const double *r2 = a.fac + it.r2off;
   const double *c02 = a.fac + it.c02off;
+  const unsigned rbytes = (unsigned)(M * RSTRIDE * sizeof(double));
+  const unsigned zbytes = (unsigned)(Nz * ZSTRIDE * sizeof(double));
+  const int J = it.J;
+  const long long total_it = (long long)a.nsteps * J;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // Factor tables of ADI iteration c (c counts iterations over all steps) go to
+  // buffer c & 1 by one bulk copy per table; iteration c + 1 is fetched while
+  // iteration c computes.
+  auto issue = [&](long long c) {
+    const int jt = (int)(c % J), buf = (int)(c & 1);
+    mbar_expect(&bar[buf], rbytes + zbytes);
+    bulk_g2s(RB0 + buf * rlen, a.fac + it.roff + (size_t)jt * M * RSTRIDE, rbytes, &bar[buf]);
+    bulk_g2s(ZB0 + buf * zlen, a.fac + it.zoff + (size_t)jt * Nz * ZSTRIDE, zbytes, &bar[buf]);
+  };
+  if (tid == 0) issue(0);
+  bool timed_out = false;
 
   const double *Xsrc = a.Xin;
+  long long c = 0;
   for (int step = 0; step < a.nsteps; ++step) {
     const double *Gs = a.G ? a.G + (size_t)step * a.gstride : nullptr;
     // Right side of eq. HelmholtzMatEqn, E = trunc(R_2 (X + kappa g) C02^T), in two
     // banded passes: T1 = (X + kappa g) C02^T on the class rows, then E = R_2 T1.
     for (int e = tid; e < it.Mfull * W; e += nth) {
-      const int ap = e / W, c = e - ap * W;
-      const int sl = c / Nz, b = c - sl * Nz;
+      const int ap = e / W, cc = e - ap * W;
+      const int sl = cc / Nz, b = cc - sl * Nz;
       const int i = it.pr + 2 * ap, j = it.pz + 2 * b;
       const size_t base = (size_t)(it.s0 + sl) * slice + (size_t)i * n;
       double acc = 0.0;
@@ -149,33 +256,40 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
           acc = fma(c02[b * C02STRIDE + t], z, acc);
         }
       }
-      S[(size_t)ap * ld + c] = acc;
+      S[ap * ld + cc] = acc;
     }
     __syncthreads();
     for (int e = tid; e < M * W; e += nth) {
-      const int aa = e / W, c = e - aa * W;
+      const int aa = e / W, cc = e - aa * W;
       double acc = 0.0;
 #pragma unroll
       for (int s = -1; s <= 3; ++s) {
         const int q = aa + s;
-        if (q >= 0 && q < it.Mfull) acc = fma(r2[aa * R2STRIDE + s + 1], S[(size_t)q * ld + c], acc);
+        if (q >= 0 && q < it.Mfull) acc = fma(r2[aa * R2STRIDE + s + 1], S[q * ld + cc], acc);
       }
-      Fa[(size_t)aa * ld + c] = acc;
+      Fa[aa * ld + cc] = acc;
     }
     __syncthreads();
 
     // Algorithm 1, J iterations, from X_0 = 0.
-    for (int jt = 0; jt < it.J; ++jt) {
-      const double *rsrc = a.fac + it.roff + (size_t)jt * M * RSTRIDE;
-      const double *zsrc = a.fac + it.zoff + (size_t)jt * Nz * ZSTRIDE;
-      for (int e = tid; e < M * RSTRIDE; e += nth) RB[e] = rsrc[e];
-      for (int e = tid; e < Nz * ZSTRIDE; e += nth) ZB[e] = zsrc[e];
-      __syncthreads();
-      if (tid < W) radial_sweep(S + tid, Fa + tid, ld, RB, M, jt == 0);
+    for (int jt = 0; jt < J; ++jt, ++c) {
+      const int buf = (int)(c & 1);
+      if (tid == 0 && c + 1 < total_it) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(c + 1);
+      }
+      if (!mbar_wait(&bar[buf], (unsigned)((c >> 1) & 1))) timed_out = true;
+      const double *RB = RB0 + buf * rlen;
+      const double *ZB = ZB0 + buf * zlen;
+      if (tid < W) {
+        if (jt == 0) radial_sweep<true>(S + tid, Fa + tid, ld, RB, M);
+        else radial_sweep<false>(S + tid, Fa + tid, ld, RB, M);
+      }
       __syncthreads();
       if (tid < nsl * M) {
         const int sl = tid / M, aa = tid - sl * M;
-        vertical_sweep(S + (size_t)aa * ld + sl * Nz, ZB, Nz, jt + 1 == it.J);
+        if (jt + 1 == J) vertical_sweep<true>(S + aa * ld + sl * Nz, ZB, Nz);
+        else vertical_sweep<false>(S + aa * ld + sl * Nz, ZB, Nz);
       }
       __syncthreads();
     }
@@ -190,10 +304,10 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
       const double *Ys = S + sl * Nz;
       const bool r0 = ap - 1 >= 0, r1 = ap < M, c0 = b - 1 >= 0, c1 = b < Nz;
       double x = 0.0;
-      if (r0 && c0) x += Ys[(size_t)(ap - 1) * ld + b - 1];
-      if (r0 && c1) x -= Ys[(size_t)(ap - 1) * ld + b];
-      if (r1 && c0) x -= Ys[(size_t)ap * ld + b - 1];
-      if (r1 && c1) x += Ys[(size_t)ap * ld + b];
+      if (r0 && c0) x += Ys[(ap - 1) * ld + b - 1];
+      if (r0 && c1) x -= Ys[(ap - 1) * ld + b];
+      if (r1 && c0) x -= Ys[ap * ld + b - 1];
+      if (r1 && c1) x += Ys[ap * ld + b];
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * ap) * n + it.pz + 2 * b;
       a.Xout[o] = x;
       if (ck) ck[o] = x;
@@ -211,13 +325,21 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
     __syncthreads();
     Xsrc = a.Xout;
   }
+  if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(adi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  adi_kernel<<<a.nitems, threads, smem, st>>>(a);
+  cudaError_t e;
+  if (a.use_smem) {
+    e = cudaFuncSetAttribute(adi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_kernel<true><<<a.nitems, threads, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(adi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_kernel<false><<<a.nitems, threads, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -29,7 +29,10 @@ struct AdiArgs {
   int ld;                  // leading dimension of the work arrays (odd)
   int smem_rows;           // rows of the S array (max Mfull)
   int maxM, maxNz;         // band table sizes in shared memory
+  int *err;                // device status word (CYL_ERR_TIMEOUT on a bounded-wait timeout)
 };
+
+constexpr int CYL_ERR_TIMEOUT = 4;
 
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem);
 

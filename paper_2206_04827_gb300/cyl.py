@@ -38,6 +38,7 @@ _sig = {
     'cyl_heat_adjoint': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp, _vp]),
     'cyl_status_string': (ctypes.c_char_p, [ctypes.c_int]),
+    'cyl_sync': (ctypes.c_int, [_vp]),
     'cyl_plan_shifts': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        _c_double_p, _c_double_p, _c_double_p]),
     'cyl_plan_operator': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -147,6 +148,10 @@ class Plan:
                                      _ptr(dL_dT0, 'dL_dT0', self.N), _ptr(dL_dg, 'dL_dg', self.N),
                                      _ptr(dL_dalpha, 'dL_dalpha', 1)), 'cyl_heat_adjoint')
         return dL_dT0
+
+    def sync(self):
+        """Wait for the plan's stream; raise on a device-side timeout or CUDA error."""
+        _check(_lib.cyl_sync(self._h), 'cyl_sync')
 
     # -- host introspection ---------------------------------------------------
     def grid(self):

@@ -60,6 +60,7 @@ def test_poisson_coeffs_match_oracle(cyl, m, n, p):
     F = inputs.smooth_coeffs(p, m, n, 1.2, np.random.default_rng(7 * m + n))
     plan = cyl.Plan(m, n, p, adi_tol=1e-14)
     u = plan.poisson(dev(F), torch.empty(p, m, n, dtype=torch.float64, device='cuda'), cyl.COEFFS)
+    plan.sync()
     assert relerr(host(u), oheat.poisson(F)) <= TOL_SOLVE
 
 
@@ -105,6 +106,7 @@ def test_heat_steps_match_oracle(cyl, m, n, p, steps):
     plan = cyl.Plan(m, n, p, alpha, dt, 1e-14, poisson=False, heat=True)
     T = dev(X0)
     plan.heat_step(T, dev(g), steps)
+    plan.sync()
     assert relerr(host(T), oheat.heat_steps(X0, g, alpha, dt, steps)) <= TOL_SOLVE
 
 
