@@ -161,6 +161,36 @@ cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
  */
 cyl_status cyl_sync(cyl_plan_t plan);
 
+/*
+ * cyl_vals2coeffs_noalloc -- the values -> coefficients transform of
+ * cyl_vals2coeffs without a plan and without any allocation.  The paper has
+ * no counterpart; this entry point exists for callers that cannot allocate
+ * device memory: code running while a CUDA graph is captured (cudaMalloc is
+ * not allowed there), hosts whose own pool owns all device memory, and
+ * loops that must never enter an allocator.  cyl_plan allocates, so such
+ * callers cannot use the planned entry points.
+ *
+ *   n_r, n_z     >= 2; n_theta even and >= 2.
+ *   vals, coeffs caller-owned device arrays of n_r*n_z*n_theta float64
+ *                ([p][m][n] layout as above); they may alias.
+ *   stream       cudaStream_t to run on (NULL = legacy default stream).
+ *
+ * Scratch comes from one fixed array of CYL_NOALLOC_SCRATCH_DOUBLES float64
+ * (64 MiB) that every device context loading the library holds until the
+ * process exits.  A call needs 2 N + n_r^2 + n_z^2 + n_theta^2 doubles of it
+ * (N = n_r n_z n_theta; e.g. 160^3 fits, 170^3 does not); larger problems
+ * return CYL_EINVAL and launch nothing.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call uses
+ * the same array and fully rewrites what it reads, so nothing needs clearing
+ * between calls, but calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race on the array and give wrong
+ * results: serialise them.  Calls no cudaMalloc or cudaFree.
+ */
+#define CYL_NOALLOC_SCRATCH_DOUBLES (1 << 23)
+cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, const double *vals, double *coeffs,
+                                   void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *cyl_status_string(cyl_status s);
 
