@@ -134,23 +134,35 @@ cyl_status cyl_heat_step(cyl_plan_t plan, double *T, const double *g, long long 
  * cyl_heat_adjoint -- reverse-mode derivatives of a scalar loss L(T_N) of the
  * BDF1 run that cyl_heat_step(T0, g, g_step_stride, nsteps) computes.  Not in
  * the paper: the exact transpose of that linear stepping map, i.e. the
- * transposed Sylvester solves run backward through the steps, with the states
- * recomputed from checkpoints every ckpt_every steps.
+ * transposed Sylvester solves (ADI on A^T X B + C^T X D = E with the same
+ * shifts) run backward through the steps.  dL/dalpha uses the forward states,
+ * recomputed segment by segment from checkpoints every ckpt_every steps:
+ * dL/dalpha = sum_n <dL/dT_n, T_{n+1} - T_n - dt g_n> / alpha, an identity of
+ * the BDF1 step (the alpha-derivative of the solve is (E - C Y B^T) / alpha).
  *
- *   T0, g, g_step_stride, nsteps   as for cyl_heat_step (T0 is not modified).
+ *   T0, g, g_step_stride, nsteps   as for cyl_heat_step (T0 is not modified;
+ *               T0 may be NULL when dL_dalpha is NULL).
  *   dL_dTN      device, N float64: dL/dT_N (coefficient layout).
- *   dL_dT0      device, N float64 output.
+ *   dL_dT0      device, N float64 output (may alias dL_dTN).
  *   dL_dg       NULL, or device output shaped like g: N float64 when
  *               g_step_stride = 0 (summed over steps), else nsteps arrays at
  *               stride g_step_stride.
  *   dL_dalpha   NULL, or device pointer to ONE float64 output.
- *   ckpt_every  >= 1; states are recomputed in segments of this length.
- * Needs CYL_WITH_HEAT.
+ *   ckpt_every  >= 1; states are recomputed in segments of this length
+ *               (a value >= nsteps stores every state of the run).
+ *   workspace   device memory of at least cyl_heat_adjoint_workspace() bytes
+ *               (none is needed when dL_dalpha is NULL).
+ * Cost: one forward pass for the checkpoints, one for the recomputation and
+ * one transposed pass (only the last without dL_dalpha).  Needs CYL_WITH_HEAT.
  */
 cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
                             long long g_step_stride, int nsteps, int ckpt_every,
                             const double *dL_dTN, double *dL_dT0, double *dL_dg,
-                            double *dL_dalpha);
+                            double *dL_dalpha, void *workspace, size_t workspace_bytes);
+
+/* Bytes of device workspace cyl_heat_adjoint needs (0 when need_alpha is 0). */
+cyl_status cyl_heat_adjoint_workspace(cyl_plan_t plan, int nsteps, int ckpt_every, int need_alpha,
+                                      size_t *bytes);
 
 /*
  * cyl_sync -- wait for every call queued on the plan's stream, then report

@@ -76,11 +76,13 @@ def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=Fa
     return (X, traj) if return_all else X
 
 
-def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN):
+def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None):
     """Reverse-mode derivatives of L(X_N) for the BDF1 stepping above.
 
     Returns (dL/dX0, dL/dg, dL/dalpha); dL/dg has the shape of g (summed over
-    the steps when g is one constant array).
+    the steps when g is one constant array).  With ``slices`` only those
+    half-complex slices are processed (slices are independent), and dL/dalpha
+    holds their contribution only.
 
     Step map per slice: E = Rhs(X_n + kappa g_n), Y = Sylv^-1 E, X_{n+1} = S Y S^T,
     with Sylv(Y) = A Y B^T + C Y D^T, A = C - kappa alpha Lr, D = -kappa alpha D2z.
@@ -92,14 +94,15 @@ def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN):
     sys_ = _systems(m, n, p, 'heat', kappa * alpha)
     g = np.asarray(g, dtype=np.float64)
     const_g = g.ndim == 3
-    _, traj = heat_steps(X0, g, alpha, dt, nsteps, return_all=True)
+    _, traj = heat_steps(X0, g, alpha, dt, nsteps, slices=slices, return_all=True)
+    todo = range(p) if slices is None else slices
     lam = np.array(dL_dXN, dtype=np.float64, copy=True)
     dg = np.zeros_like(g)
     dalpha = 0.0
     for step in reversed(range(nsteps)):
         Xnext = traj[step + 1]
         lam_prev = np.zeros_like(lam)
-        for s in range(p):
+        for s in todo:
             ms, bs = sys_[slice_wavenumber(s, p)]
             mu = ms.expand_T(lam[s])
             Lam = bs.solve_T(mu)

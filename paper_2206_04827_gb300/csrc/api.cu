@@ -32,6 +32,7 @@ struct cyl_plan_s {
   double *d_W[6] = {};          // Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i
   double *d_tmp[3] = {};        // N-element scratch arrays
   int *d_err = nullptr;         // device status word written by bounded waits
+  double *d_apart = nullptr;    // per-item partial sums of the alpha gradient
   size_t N = 0;
 };
 
@@ -55,6 +56,7 @@ void free_device(cyl_plan_s *P) {
   for (auto &p : P->d_W) cudaFree(p);
   for (auto &p : P->d_tmp) cudaFree(p);
   cudaFree(P->d_err);
+  cudaFree(P->d_apart);
 }
 
 cyl_status from_cuda(cudaError_t e) {
@@ -83,6 +85,27 @@ cyl_status coeffs2vals_impl(cyl_plan_s *P, const double *coeffs, double *vals) {
   if ((e = cyl::launch_axis_matvec(P->d_tmp[0], P->d_tmp[1], P->d_W[1], p, (int)m, n, P->st)) != cudaSuccess)
     return from_cuda(e);
   return from_cuda(cyl::launch_axis_matvec(P->d_tmp[1], vals, P->d_W[3], p * m, (int)n, 1, P->st));
+}
+
+cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
+  cyl::AdiArgs a{};
+  a.items = P->d_items[kind];
+  a.nitems = P->nitems[kind];
+  a.fac = P->d_fac;
+  a.m = P->hp.m;
+  a.n = P->hp.n;
+  a.p = P->hp.p;
+  a.zero_other = (P->hp.flags & CYL_BOTH_PARITIES) ? 0 : 1;
+  a.gwork = P->d_gwork;
+  a.gwork_per_item = P->gwork_per_item;
+  a.use_smem = P->use_smem[kind];
+  a.ld = P->ld;
+  a.smem_rows = P->smem_rows;
+  a.maxM = P->maxM;
+  a.maxNz = P->maxNz;
+  a.err = P->d_err;
+  a.ckpt_every = 1;
+  return a;
 }
 
 cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
@@ -170,18 +193,18 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   P->smem_rows = std::max(h.Mfull[0], h.Mfull[1]);
   int maxW = 0;
   for (int kind = 0; kind < 2; ++kind)
-    for (const Item &it : h.kind[kind].items) maxW = std::max(maxW, it.nsl * it.Nz);
+    for (const Item &it : h.kind[kind].items) maxW = std::max(maxW, it.nsl * it.Nzfull);
   P->ld = std::max(1, maxW) | 1;
   for (int kind = 0; kind < 2; ++kind) {
     int thr = 32;
     for (const Item &it : h.kind[kind].items) thr = std::max(thr, std::max(it.nsl * it.Nz, it.nsl * it.M));
-    P->threads[kind] = std::min(1024, (thr + 31) / 32 * 32);
+    P->threads[kind] = (thr + 31) / 32 * 32;
     const bool fits = !(flags & CYL_FORCE_GLOBAL) &&
                       cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, true) <= kSmemLimit;
     P->use_smem[kind] = fits ? 1 : 0;
     P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, fits);
   }
-  if (P->threads[0] > 1024 || P->threads[1] > 1024) {
+  if (P->threads[0] > 512 || P->threads[1] > 512) {
     delete P;
     return CYL_EINVAL;
   }
@@ -200,6 +223,7 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc((void **)&P->d_tmp[i], P->N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_apart, std::max(1, P->nitems[1]) * sizeof(double));
   if (e == cudaSuccess && !(P->use_smem[0] && P->use_smem[1])) {
     P->gwork_per_item = ((long long)P->smem_rows * P->ld + (long long)P->maxM * P->ld + 31) / 32 * 32;
     const int maxItems = std::max(P->nitems[0], P->nitems[1]);
@@ -259,13 +283,81 @@ cyl_status cyl_heat_step(cyl_plan_t P, double *T, const double *g, long long g_s
   return run_adi(P, 1, T, T, g, P->hp.dt, g ? g_step_stride : 0, nsteps, ckpt, ckpt_every);
 }
 
+static size_t adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, bool need_alpha) {
+  if (!need_alpha || nsteps <= 0) return 0;
+  const long long c = std::min(ckpt_every, nsteps);
+  const long long nseg = (nsteps + c - 1) / c;
+  // checkpoints X_0, X_c, ..., one segment of states X_{s c} .. X_{s c + c}, one work state
+  return (size_t)(nseg + (c + 1) + 1) * P->N;
+}
+
+cyl_status cyl_heat_adjoint_workspace(cyl_plan_t P, int nsteps, int ckpt_every, int need_alpha, size_t *bytes) {
+  if (!P || !bytes || nsteps < 0 || ckpt_every < 1) return CYL_EINVAL;
+  *bytes = adjoint_workspace_doubles(P, nsteps, ckpt_every, need_alpha != 0) * sizeof(double);
+  return CYL_OK;
+}
+
 cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, long long g_step_stride, int nsteps,
                             int ckpt_every, const double *dL_dTN, double *dL_dT0, double *dL_dg,
-                            double *dL_dalpha) {
-  (void)T0; (void)g; (void)g_step_stride; (void)nsteps; (void)ckpt_every; (void)dL_dTN; (void)dL_dT0;
-  (void)dL_dg; (void)dL_dalpha;
-  if (!P) return CYL_EINVAL;
-  return CYL_ESTATE;
+                            double *dL_dalpha, void *workspace, size_t workspace_bytes) {
+  if (!P || !dL_dTN || !dL_dT0 || nsteps < 0 || ckpt_every < 1 || g_step_stride < 0) return CYL_EINVAL;
+  if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
+  if (dL_dalpha && !T0) return CYL_EINVAL;
+  if (P->host_only || !P->hp.kind[1].built) return CYL_ESTATE;
+  const size_t need = adjoint_workspace_doubles(P, nsteps, ckpt_every, dL_dalpha != nullptr);
+  if (need && (!workspace || workspace_bytes < need * sizeof(double))) return CYL_EINVAL;
+  const size_t N = P->N;
+  const double kappa = P->hp.dt;
+  cudaError_t e = cudaMemcpyAsync(dL_dT0, dL_dTN, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+  if (e == cudaSuccess && dL_dg && g_step_stride == 0) e = cudaMemsetAsync(dL_dg, 0, N * sizeof(double), P->st);
+  if (e == cudaSuccess && dL_dalpha)
+    e = cudaMemsetAsync(P->d_apart, 0, std::max(1, P->nitems[1]) * sizeof(double), P->st);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (nsteps == 0) {
+    if (dL_dalpha) return from_cuda(cudaMemsetAsync(dL_dalpha, 0, sizeof(double), P->st));
+    return CYL_OK;
+  }
+  cyl::AdiArgs a = adi_args(P, 1);
+  cyl::AdjointArgs adj{};
+  adj.lam = dL_dT0;
+  adj.G = g;
+  adj.gstride = g ? g_step_stride : 0;
+  adj.dg = dL_dg;
+  adj.dg_stride = g_step_stride;
+  adj.kappa = kappa;
+  if (!dL_dalpha) {
+    // the stepping map is linear in (X_0, g): no forward states are needed
+    adj.n_lo = 0;
+    adj.n_hi = nsteps;
+    return from_cuda(cyl::launch_adjoint(a, adj, P->threads[1], P->smem[1], P->st));
+  }
+  const int c = std::min(ckpt_every, nsteps);
+  const int nseg = (nsteps + c - 1) / c;
+  double *ck = static_cast<double *>(workspace);       // nseg slots
+  double *seg = ck + (size_t)nseg * N;                  // c + 1 slots
+  double *work = seg + (size_t)(c + 1) * N;             // 1 slot
+  e = cudaMemcpyAsync(ck, T0, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+  if (e != cudaSuccess) return from_cuda(e);
+  cyl_status s;
+  if (nseg > 1) {                                       // checkpoints X_c, X_2c, ... (ck slot s = X_{s c})
+    s = run_adi(P, 1, T0, work, g, kappa, g ? g_step_stride : 0, (nseg - 1) * c, ck, c);
+    if (s != CYL_OK) return s;
+  }
+  adj.traj = seg;
+  adj.alpha_part = P->d_apart;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int n_lo = sgi * c, n_hi = std::min(n_lo + c, nsteps);
+    e = cudaMemcpyAsync(seg, ck + (size_t)sgi * N, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    const double *gseg = g ? g + (size_t)n_lo * g_step_stride : nullptr;
+    s = run_adi(P, 1, seg, work, gseg, kappa, g ? g_step_stride : 0, n_hi - n_lo, seg, 1);
+    if (s != CYL_OK) return s;
+    adj.n_lo = n_lo;
+    adj.n_hi = n_hi;
+    e = cyl::launch_adjoint(a, adj, P->threads[1], P->smem[1], P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return from_cuda(cyl::launch_sum_partials(P->d_apart, P->nitems[1], 1.0 / P->hp.alpha, dL_dalpha, P->st));
 }
 
 cyl_status cyl_sync(cyl_plan_t P) {

@@ -69,91 +69,133 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 //   vertical: X_{j+1} = Z (D + qB)^-T,  U' = X_{j+1} (D + p'B)^T
 // which is the paper's two half-steps (with the signs corrected so that the
 // fixed point solves A X B^T + C X D^T = E) after eliminating the C solve.
+// TRANS selects the transposed system A^T X B + C^T X D = E (adjoint), whose
+// factor records have the same size with the band orientations swapped.
 //
 // Every sweep loads the operands of the next row (column) one step ahead
 // into registers: with one warp per SM sub-partition an exposed shared-memory
 // latency idles the FP64 pipe, which is the only resource that matters here.
-template <bool FIRST>
+template <int K>
+__device__ __forceinline__ double comp(const double2 *a) {
+  return (K & 1) ? a[K >> 1].y : a[K >> 1].x;
+}
+
+template <bool FIRST, bool TRANS>
 __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const double *__restrict__ Fc, int ld,
                                              const double *__restrict__ RB, int M) {
-  double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0, w4 = 0.0;
-  if (!FIRST) {
-    if (M > 0) w2 = col[0];
-    if (M > 1) w3 = col[ld];
-    if (M > 2) w4 = col[2 * ld];
-  }
-  double fn = M > 0 ? Fc[0] : 0.0;
-  double un = (!FIRST && M > 3) ? col[3 * ld] : 0.0;
+  constexpr int LO = TRANS ? 3 : 2, HI = TRANS ? 2 : 3;     // apply band offsets [-LO, HI]
+  constexpr int LBW = TRANS ? 3 : 2, UBW = TRANS ? 2 : 3;   // L and U bandwidths
+  constexpr int NF = (6 + LBW + 1) / 2;                     // double2 words read going down
+  constexpr int B0 = (6 + LBW) / 2;                         // first double2 word read going up
+  constexpr int NB = RSTRIDE / 2 - B0;
   const double2 *rb2 = reinterpret_cast<const double2 *>(RB);
-  double2 n01 = rb2[0], n23 = rb2[1], n45 = rb2[2], n67 = rb2[3];
-  double y1 = 0.0, y2 = 0.0;
+  double w[LO + HI + 1];
+#pragma unroll
+  for (int k = 0; k <= LO + HI; ++k) w[k] = 0.0;
+  if (!FIRST) {
+#pragma unroll
+    for (int o = 0; o < HI; ++o) w[LO + o] = (o < M) ? col[o * ld] : 0.0;
+  }
+  double fn = Fc[0];
+  double un = (!FIRST && HI < M) ? col[HI * ld] : 0.0;
+  double2 nrec[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) nrec[k] = rb2[k];
+  double y[LBW];
+#pragma unroll
+  for (int k = 0; k < LBW; ++k) y[k] = 0.0;
   for (int i = 0; i < M; ++i) {
-    const double f = fn, w5 = un;
-    const double2 a01 = n01, a23 = n23, a45 = n45, a67 = n67;
+    const double f = fn;
+    double2 rec[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) rec[k] = nrec[k];
+    if (!FIRST) w[LO + HI] = un;
     if (i + 1 < M) {
       fn = Fc[(i + 1) * ld];
-      if (!FIRST) un = (i + 4 < M) ? col[(i + 4) * ld] : 0.0;
+      if (!FIRST) un = (i + 1 + HI < M) ? col[(i + 1 + HI) * ld] : 0.0;
       const double2 *nx = rb2 + (i + 1) * (RSTRIDE / 2);
-      if (!FIRST) { n01 = nx[0]; n23 = nx[1]; n45 = nx[2]; }
-      n67 = nx[3];
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (!FIRST || 2 * k + 1 >= 6) nrec[k] = nx[k];
     }
     double acc = f;
     if (!FIRST) {
-      acc = fma(a01.x, w0, acc);
-      acc = fma(a01.y, w1, acc);
-      acc = fma(a23.x, w2, acc);
-      acc = fma(a23.y, w3, acc);
-      acc = fma(a45.x, w4, acc);
-      acc = fma(a45.y, w5, acc);
-      w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5;
+      acc = fma(comp<0>(rec), w[0], acc);
+      acc = fma(comp<1>(rec), w[1], acc);
+      acc = fma(comp<2>(rec), w[2], acc);
+      acc = fma(comp<3>(rec), w[3], acc);
+      acc = fma(comp<4>(rec), w[4], acc);
+      acc = fma(comp<5>(rec), w[5], acc);
+#pragma unroll
+      for (int k = 0; k < LO + HI; ++k) w[k] = w[k + 1];
     }
-    acc = fma(a67.x, y1, acc);
-    acc = fma(a67.y, y2, acc);
+    acc = fma(comp<6>(rec), y[0], acc);
+    acc = fma(comp<7>(rec), y[1], acc);
+    if (LBW == 3) acc = fma(comp<(LBW == 3 ? 8 : 7)>(rec), y[LBW - 1], acc);
     col[i * ld] = acc;
-    y2 = y1;
-    y1 = acc;
+#pragma unroll
+    for (int l = LBW - 1; l > 0; --l) y[l] = y[l - 1];
+    y[0] = acc;
   }
-  double z1 = 0.0, z2 = 0.0, z3 = 0.0;
-  if (M <= 0) return;
+  double z[UBW];
+#pragma unroll
+  for (int u = 0; u < UBW; ++u) z[u] = 0.0;
   double yn = col[(M - 1) * ld];
-  double2 b89 = rb2[(M - 1) * (RSTRIDE / 2) + 4], bab = rb2[(M - 1) * (RSTRIDE / 2) + 5];
+  double2 nb[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) nb[k] = rb2[(M - 1) * (RSTRIDE / 2) + B0 + k];
   for (int i = M - 1; i >= 0; --i) {
-    const double y = yn;
-    const double2 c89 = b89, cab = bab;
+    const double yv = yn;
+    double2 cb[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) cb[k] = nb[k];
     if (i > 0) {
       yn = col[(i - 1) * ld];
-      b89 = rb2[(i - 1) * (RSTRIDE / 2) + 4];
-      bab = rb2[(i - 1) * (RSTRIDE / 2) + 5];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) nb[k] = rb2[(i - 1) * (RSTRIDE / 2) + B0 + k];
     }
-    double acc = fma(c89.x, z1, y);
-    acc = fma(c89.y, z2, acc);
-    acc = fma(cab.x, z3, acc);
-    const double zi = acc * cab.y;
+    double acc = fma(comp<6 + LBW - 2 * B0>(cb), z[0], yv);
+    acc = fma(comp<7 + LBW - 2 * B0>(cb), z[1], acc);
+    if (UBW == 3) acc = fma(comp<(UBW == 3 ? 8 + LBW - 2 * B0 : 7 + LBW - 2 * B0)>(cb), z[UBW - 1], acc);
+    const double zi = acc * comp<11 - 2 * B0>(cb);
     col[i * ld] = zi;
-    z3 = z2; z2 = z1; z1 = zi;
+#pragma unroll
+    for (int u = UBW - 1; u > 0; --u) z[u] = z[u - 1];
+    z[0] = zi;
   }
 }
 
-template <bool LAST>
+template <bool LAST, bool TRANS>
 __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz) {
-  if (Nz <= 0) return;
-  double w = 0.0;
-  double rn = row[0], cn = ZB[0];
+  constexpr int LB = TRANS ? 2 : 1;                         // L bandwidth (U: 3 - LB)
+  constexpr int ALO = TRANS ? 2 : 1;                        // apply offsets [-ALO, 3 - ALO]
+  const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
+  double wq[LB];
+#pragma unroll
+  for (int l = 0; l < LB; ++l) wq[l] = 0.0;
+  double rn = row[0];
+  double2 cn = z2p[0];
   for (int b = 0; b < Nz; ++b) {
-    const double r = rn, c = cn;
+    const double r = rn;
+    const double2 c = cn;
     if (b + 1 < Nz) {
       rn = row[b + 1];
-      cn = ZB[(b + 1) * ZSTRIDE];
+      cn = z2p[(b + 1) * 4];
     }
-    w = fma(c, w, r);
+    double w = fma(c.x, wq[0], r);
+    if (LB == 2) w = fma(c.y, wq[LB - 1], w);
     row[b] = w;
+#pragma unroll
+    for (int l = LB - 1; l > 0; --l) wq[l] = wq[l - 1];
+    wq[0] = w;
   }
-  const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
-  double x1 = 0.0, x2 = 0.0, x3 = 0.0;
+  double x1 = 0.0, x2 = 0.0, x3 = 0.0;                      // x_{b+1}, x_{b+2}, x_{b+3}
   double2 p01 = z2p[(Nz - 1) * 4], p23 = z2p[(Nz - 1) * 4 + 1], p45, p67;
   if (!LAST) { p45 = z2p[(Nz - 1) * 4 + 2]; p67 = z2p[(Nz - 1) * 4 + 3]; }
   double wn = row[Nz - 1];
-  double ap0 = 0.0, ap1 = 0.0, ap2 = 0.0, ap3 = 0.0;   // apply band of column b + 1
+  double2 q45[ALO], q67[ALO];                               // apply records of columns b+1 .. b+ALO
+#pragma unroll
+  for (int t = 0; t < ALO; ++t) { q45[t] = make_double2(0.0, 0.0); q67[t] = make_double2(0.0, 0.0); }
   for (int b = Nz - 1; b >= 0; --b) {
     const double wb = wn;
     const double2 c01 = p01, c23 = p23;
@@ -165,33 +207,119 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
       p23 = z2p[(b - 1) * 4 + 1];
       if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
     }
-    double v = fma(c01.y, x1, wb);
-    v = fma(c23.x, x2, v);
-    const double xb = v * c23.y;
+    double v, xb;
+    if (TRANS) {            // [0..1] -L, [2] -U, [3] 1/U_cc
+      v = fma(c23.x, x1, wb);
+      xb = v * c23.y;
+    } else {                // [0] -L, [1..2] -U, [3] 1/U_cc
+      v = fma(c01.y, x1, wb);
+      v = fma(c23.x, x2, v);
+      xb = v * c23.y;
+    }
     if (LAST) {
       row[b] = xb;
     } else {
-      if (b + 1 < Nz) {
-        double u = ap0 * xb;
-        u = fma(ap1, x1, u);
-        u = fma(ap2, x2, u);
-        u = fma(ap3, x3, u);
-        row[b + 1] = u;
+      if (b + ALO < Nz) {
+        const double2 a45 = q45[ALO - 1], a67 = q67[ALO - 1];
+        double u = a45.x * xb;
+        u = fma(a45.y, x1, u);
+        u = fma(a67.x, x2, u);
+        u = fma(a67.y, x3, u);
+        row[b + ALO] = u;
       }
-      ap0 = c45.x; ap1 = c45.y; ap2 = c67.x; ap3 = c67.y;
+#pragma unroll
+      for (int t = ALO - 1; t > 0; --t) { q45[t] = q45[t - 1]; q67[t] = q67[t - 1]; }
+      q45[0] = c45;
+      q67[0] = c67;
     }
     x3 = x2; x2 = x1; x1 = xb;
   }
-  if (!LAST) {
-    double u = ap1 * x1;
-    u = fma(ap2, x2, u);
-    u = fma(ap3, x3, u);
-    row[0] = u;
+  if (!LAST) {              // columns 0 .. ALO-1 (x_{-1}, x_{-2} = 0); q[t] holds column t
+    if (ALO == 1) {
+      double u = q45[0].y * x1;
+      u = fma(q67[0].x, x2, u);
+      u = fma(q67[0].y, x3, u);
+      row[0] = u;
+    } else {
+      double u1 = q45[ALO - 1].y * x1;
+      u1 = fma(q67[ALO - 1].x, x2, u1);
+      u1 = fma(q67[ALO - 1].y, x3, u1);
+      if (Nz > 1) row[1] = u1;
+      double u0 = q67[0].x * x1;
+      u0 = fma(q67[0].y, x2, u0);
+      row[0] = u0;
+    }
+  }
+}
+
+// J iterations of Algorithm 1 on one item from X_0 = 0: right side in Fa,
+// result in S.  Factor tables of iteration c (counted over all steps of the
+// launch) arrive in buffer c & 1 by TMA bulk copies issued one iteration ahead.
+struct AdiShared {
+  double *RB0, *ZB0;
+  int rlen, zlen;
+  unsigned long long *bar;
+};
+
+template <bool TRANS>
+__device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs &a, const Item &it, long long c) {
+  const int jt = (int)(c % it.J), buf = (int)(c & 1);
+  const unsigned rbytes = (unsigned)(it.M * RSTRIDE * sizeof(double));
+  const unsigned zbytes = (unsigned)(it.Nz * ZSTRIDE * sizeof(double));
+  const long long roff = TRANS ? it.roffT : it.roff, zoff = TRANS ? it.zoffT : it.zoff;
+  mbar_expect(&sh.bar[buf], rbytes + zbytes);
+  bulk_g2s(sh.RB0 + buf * sh.rlen, a.fac + roff + (size_t)jt * it.M * RSTRIDE, rbytes, &sh.bar[buf]);
+  bulk_g2s(sh.ZB0 + buf * sh.zlen, a.fac + zoff + (size_t)jt * it.Nz * ZSTRIDE, zbytes, &sh.bar[buf]);
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void adi_iterations(const AdiShared &sh, const AdiArgs &a, const Item &it, double *S,
+                                               double *Fa, long long &c, long long total_it, bool &timed_out) {
+  const int tid = threadIdx.x, M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, ld = a.ld, J = it.J;
+  for (int jt = 0; jt < J; ++jt, ++c) {
+    const int buf = (int)(c & 1);
+    if (tid == 0 && c + 1 < total_it) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tables<TRANS>(sh, a, it, c + 1);
+    }
+    if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1))) timed_out = true;
+    const double *RB = sh.RB0 + buf * sh.rlen;
+    const double *ZB = sh.ZB0 + buf * sh.zlen;
+    if (tid < W) {
+      if (jt == 0) radial_sweep<true, TRANS>(S + tid, Fa + tid, ld, RB, M);
+      else radial_sweep<false, TRANS>(S + tid, Fa + tid, ld, RB, M);
+    }
+    __syncthreads();
+    if (tid < nsl * M) {
+      const int sl = tid / M, aa = tid - sl * M;
+      if (jt + 1 == J) vertical_sweep<true, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
+      else vertical_sweep<false, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
+    }
+    __syncthreads();
   }
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
+__device__ __forceinline__ void setup_shared(const AdiArgs &a, AdiShared &sh, double *&S, double *&Fa, double *sm,
+                                             unsigned long long *bar) {
+  sh.rlen = a.maxM * RSTRIDE;
+  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.RB0 = sm;                          // [2][maxM * RSTRIDE]
+  sh.ZB0 = sm + 2 * sh.rlen;            // [2][maxNz * ZSTRIDE]
+  sh.bar = bar;
+  if (SMEM) S = sh.ZB0 + 2 * sh.zlen;
+  else S = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
+  Fa = S + (size_t)a.smem_rows * a.ld;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
   const Item it = a.items[blockIdx.x];
@@ -200,39 +328,13 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
   const int ld = a.ld;
   const int m = a.m, n = a.n;
   const long long slice = (long long)m * n;
-  const int rlen = a.maxM * RSTRIDE, zlen = a.maxNz * ZSTRIDE;
-  double *RB0 = sm;                       // [2][maxM * RSTRIDE]
-  double *ZB0 = sm + 2 * rlen;            // [2][maxNz * ZSTRIDE]
+  AdiShared sh;
   double *S, *Fa;
-  if (SMEM) {
-    S = ZB0 + 2 * zlen;
-  } else {
-    S = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
-  }
-  Fa = S + (size_t)a.smem_rows * ld;
+  setup_shared<SMEM>(a, sh, S, Fa, sm, bar);
   const double *r2 = a.fac + it.r2off;
   const double *c02 = a.fac + it.c02off;
-  const unsigned rbytes = (unsigned)(M * RSTRIDE * sizeof(double));
-  const unsigned zbytes = (unsigned)(Nz * ZSTRIDE * sizeof(double));
-  const int J = it.J;
-  const long long total_it = (long long)a.nsteps * J;
-
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // Factor tables of ADI iteration c (c counts iterations over all steps) go to
-  // buffer c & 1 by one bulk copy per table; iteration c + 1 is fetched while
-  // iteration c computes.
-  auto issue = [&](long long c) {
-    const int jt = (int)(c % J), buf = (int)(c & 1);
-    mbar_expect(&bar[buf], rbytes + zbytes);
-    bulk_g2s(RB0 + buf * rlen, a.fac + it.roff + (size_t)jt * M * RSTRIDE, rbytes, &bar[buf]);
-    bulk_g2s(ZB0 + buf * zlen, a.fac + it.zoff + (size_t)jt * Nz * ZSTRIDE, zbytes, &bar[buf]);
-  };
-  if (tid == 0) issue(0);
+  const long long total_it = (long long)a.nsteps * it.J;
+  if (tid == 0) issue_tables<false>(sh, a, it, 0);
   bool timed_out = false;
 
   const double *Xsrc = a.Xin;
@@ -271,28 +373,7 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
     }
     __syncthreads();
 
-    // Algorithm 1, J iterations, from X_0 = 0.
-    for (int jt = 0; jt < J; ++jt, ++c) {
-      const int buf = (int)(c & 1);
-      if (tid == 0 && c + 1 < total_it) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(c + 1);
-      }
-      if (!mbar_wait(&bar[buf], (unsigned)((c >> 1) & 1))) timed_out = true;
-      const double *RB = RB0 + buf * rlen;
-      const double *ZB = ZB0 + buf * zlen;
-      if (tid < W) {
-        if (jt == 0) radial_sweep<true>(S + tid, Fa + tid, ld, RB, M);
-        else radial_sweep<false>(S + tid, Fa + tid, ld, RB, M);
-      }
-      __syncthreads();
-      if (tid < nsl * M) {
-        const int sl = tid / M, aa = tid - sl * M;
-        if (jt + 1 == J) vertical_sweep<true>(S + aa * ld + sl * Nz, ZB, Nz);
-        else vertical_sweep<false>(S + aa * ld + sl * Nz, ZB, Nz);
-      }
-      __syncthreads();
-    }
+    adi_iterations<false>(sh, a, it, S, Fa, c, total_it, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
     const int Wf = nsl * it.Nzfull;
@@ -326,6 +407,137 @@ __global__ void __launch_bounds__(1024) adi_kernel(const AdiArgs a) {
     Xsrc = a.Xout;
   }
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+// Adjoint of the BDF1 steps n = n_hi-1 .. n_lo for one item (the transpose of
+// adi_kernel's map, step by step in reverse):
+//   mu = S_r^T lam S_z;  Lambda = (A^T . B + C^T . D)^-1 mu by the transposed ADI;
+//   lam <- R_2^T Lambda C02 (class rows < m, class columns < n);
+//   dL/dg_n = kappa lam;  dL/dalpha += <lam, X_{n+1} - X_n - kappa g_n> / alpha
+// (the last identity follows from A Y B^T + C Y D^T = E, A = C - kappa alpha L,
+// D = -kappa alpha D2:  d/dalpha of the solve is (E - C Y B^T) / alpha).
+template <bool SMEM>
+__global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, AdjointArgs g) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ double red[32];
+  const Item it = a.items[blockIdx.x];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, Wf = nsl * it.Nzfull;
+  const int ld = a.ld;
+  const int m = a.m, n = a.n;
+  const long long slice = (long long)m * n, Ntot = (long long)a.p * slice;
+  AdiShared sh;
+  double *S, *Fa;
+  setup_shared<SMEM>(a, sh, S, Fa, sm, bar);
+  const double *r2 = a.fac + it.r2off;
+  const double *c02 = a.fac + it.c02off;
+  const int nst = g.n_hi - g.n_lo;
+  const long long total_it = (long long)nst * it.J;
+  if (tid == 0) issue_tables<true>(sh, a, it, 0);
+  bool timed_out = false;
+  double apart = 0.0;
+  double *lam = g.lam;
+  long long c = 0;
+  for (int n_step = g.n_hi - 1; n_step >= g.n_lo; --n_step) {
+    // mu[a][b] = lam[a][b] - lam[a][b+1] - lam[a+1][b] + lam[a+1][b+1] (class indices)
+    for (int e = tid; e < M * W; e += nth) {
+      const int aa = e / W, cc = e - aa * W;
+      const int sl = cc / Nz, b = cc - sl * Nz;
+      const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * aa) * n + it.pz + 2 * b;
+      Fa[aa * ld + cc] = lam[o] - lam[o + 2] - lam[o + 2 * n] + lam[o + 2 * n + 2];
+    }
+    __syncthreads();
+    adi_iterations<true>(sh, a, it, S, Fa, c, total_it, timed_out);
+    // T1 = Lambda C02 on nsl * Nzfull columns: T1[a][b'] = sum_t Lambda[a][b' - t] C02[b' - t][t]
+    for (int e = tid; e < M * Wf; e += nth) {
+      const int aa = e / Wf, cc = e - aa * Wf;
+      const int sl = cc / it.Nzfull, bp = cc - sl * it.Nzfull;
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int b = bp - t;
+        if (b >= 0 && b < Nz) acc = fma(c02[b * C02STRIDE + t], S[aa * ld + sl * Nz + b], acc);
+      }
+      Fa[aa * ld + cc] = acc;
+    }
+    __syncthreads();
+    // lam_n = R_2^T T1 on all class rows; forcing gradient and alpha term
+    const double *Gn = g.G ? g.G + (size_t)n_step * g.gstride : nullptr;
+    double *dgn = g.dg ? g.dg + (size_t)n_step * g.dg_stride : nullptr;
+    const double *Xn = g.traj ? g.traj + (size_t)(n_step - g.n_lo) * Ntot : nullptr;
+    for (int e = tid; e < it.Mfull * Wf; e += nth) {
+      const int ap = e / Wf, cc = e - ap * Wf;
+      const int sl = cc / it.Nzfull, bp = cc - sl * it.Nzfull;
+      double acc = 0.0;
+#pragma unroll
+      for (int s = -1; s <= 3; ++s) {
+        const int q = ap - s;
+        if (q >= 0 && q < M) acc = fma(r2[q * R2STRIDE + s + 1], Fa[q * ld + cc], acc);
+      }
+      const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * ap) * n + it.pz + 2 * bp;
+      lam[o] = acc;
+      if (dgn) {
+        if (g.dg_stride == 0) dgn[o] += g.kappa * acc;
+        else dgn[o] = g.kappa * acc;
+      }
+      if (Xn) {
+        double d = Xn[o + Ntot] - Xn[o];
+        if (Gn) d = fma(-g.kappa, Gn[o], d);
+        apart = fma(acc, d, apart);
+      }
+    }
+    if (a.zero_other) {
+      const int po = 1 - it.pr, Mo = (m - po + 1) / 2;
+      for (int e = tid; e < Mo * Wf; e += nth) {
+        const int ap = e / Wf, cc = e - ap * Wf;
+        const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
+        const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(po + 2 * ap) * n + it.pz + 2 * b;
+        lam[o] = 0.0;
+        if (dgn && g.dg_stride != 0) dgn[o] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  if (g.alpha_part) {
+    for (int off = 16; off > 0; off >>= 1) apart += __shfl_down_sync(0xffffffffu, apart, off);
+    if ((tid & 31) == 0) red[tid >> 5] = apart;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (nth + 31) / 32; ++w) s += red[w];
+      g.alpha_part[blockIdx.x] += s;
+    }
+  }
+  if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+__global__ void sum_partials_kernel(const double *part, int n, double scale, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s * scale;
+  }
+}
+
+cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st) {
+  sum_partials_kernel<<<1, 32, 0, st>>>(part, n, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st) {
+  if (a.nitems <= 0 || g.n_hi <= g.n_lo) return cudaSuccess;
+  cudaError_t e;
+  if (a.use_smem) {
+    e = cudaFuncSetAttribute(adi_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_adjoint_kernel<true><<<a.nitems, threads, smem, st>>>(a, g);
+  } else {
+    e = cudaFuncSetAttribute(adi_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_adjoint_kernel<false><<<a.nitems, threads, smem, st>>>(a, g);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {

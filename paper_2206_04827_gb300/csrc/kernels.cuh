@@ -34,6 +34,22 @@ struct AdiArgs {
 
 constexpr int CYL_ERR_TIMEOUT = 4;
 
+// Extra arguments of one adjoint launch (steps n_hi-1 down to n_lo).
+struct AdjointArgs {
+  double *lam;             // adjoint state, in: dL/dX_{n_hi}, out: dL/dX_{n_lo} ([p][m][n])
+  const double *G;         // forcing (for the alpha term) or NULL
+  long long gstride;
+  double *dg;              // dL/dg output or NULL
+  long long dg_stride;     // 0: accumulate into one array; else per-step stride
+  const double *traj;      // X_{n_lo} .. X_{n_hi} (N each) or NULL (no alpha term)
+  double *alpha_part;      // per-item partial sums of <lam, X_{n+1} - X_n - kappa g_n>, or NULL
+  double kappa;
+  int n_lo, n_hi;
+};
+
+cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st);
+
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem);
 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st);

@@ -348,6 +348,13 @@ Band HostPlan::Lblk(int k, int pr) const { return block(recomb(full_L(m, k)), pr
 Band HostPlan::Bblk(int pz) const { return block(recomb(full_C02(n)), pz); }
 Band HostPlan::D2blk(int pz) const { return block(recomb(op_D2(n)), pz); }
 
+static Band transpose(const Band &B) {
+  Band T(B.n, B.hi, B.lo);
+  for (int i = 0; i < B.n; ++i)
+    for (int j = std::max(0, i - B.lo); j <= std::min(B.n - 1, i + B.hi); ++j) T.at(j, i) = B.get(i, j);
+  return T;
+}
+
 // Pad a block band to fixed offsets [-lo, hi] (so kernels use fixed strides).
 static Band widen(const Band &B, int lo, int hi) {
   Band W(B.n, lo, hi);
@@ -457,6 +464,24 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             F.push_back(s / LU.get(i, i));
           }
         }
+        // transposed radial factors (adjoint of the heat step)
+        long long roffT = -1;
+        if (kind == 1) {
+          roffT = (long long)F.size();
+          for (int j = 0; j < S.J; ++j) {
+            const double pj = S.p[j], qj = S.q[j], s = qj - pj;
+            Band LU = transpose(axpby(1.0, A, -pj, Cb[pr]));     // offsets -3 .. 2
+            if (!lu_inplace(LU)) return "transposed radial LU failed (zero pivot)";
+            for (int i = 0; i < M; ++i) {
+              for (int o = -3; o <= 2; ++o)
+                F.push_back((i + o >= 0 && i + o < M)
+                                ? (A.get(i + o, i) - qj * Cb[pr].get(i + o, i)) / s : 0.0);
+              for (int o = 1; o <= 3; ++o) F.push_back(i >= o ? -LU.get(i, i - o) : 0.0);
+              for (int o = 1; o <= 2; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s : 0.0);
+              F.push_back(s / LU.get(i, i));
+            }
+          }
+        }
         // vertical factors per vertical parity; items
         for (int pz = 0; pz < 2; ++pz) {
           const int Nz = hp.Nc[pz];
@@ -479,12 +504,33 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
               }
             }
           }
+          long long zoffT = -1;
+          if (kind == 1) {
+            zoffT = (long long)F.size();
+            for (int j = 0; j < S.J; ++j) {
+              Band LU = transpose(axpby(1.0, D, S.q[j], Bb[pz]));   // offsets -2 .. 1
+              if (!lu_inplace(LU)) return "transposed vertical LU failed (zero pivot)";
+              const bool last = (j + 1 == S.J);
+              const double pn = last ? 0.0 : S.p[j + 1];
+              for (int cc = 0; cc < Nz; ++cc) {
+                F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
+                F.push_back(cc >= 2 ? -LU.get(cc, cc - 2) : 0.0);
+                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) : 0.0);
+                F.push_back(1.0 / LU.get(cc, cc));
+                for (int o = -2; o <= 1; ++o) {
+                  const int l = cc + o;
+                  F.push_back((!last && l >= 0 && l < Nz) ? D.get(l, cc) + pn * Bb[pz].get(l, cc) : 0.0);
+                }
+              }
+            }
+          }
           // one item per slice group
           auto add_item = [&](int s0, int nsl) {
             Item it{};
             it.s0 = s0; it.nsl = nsl; it.k = k; it.pr = pr; it.pz = pz;
             it.M = M; it.Mfull = hp.Mfull[pr]; it.Nz = Nz; it.Nzfull = hp.Nfull[pz];
             it.J = S.J; it.roff = roff; it.zoff = zoff; it.r2off = r2off[pr]; it.c02off = c02off[pz];
+            it.roffT = roffT; it.zoffT = zoffT;
             KT.items.push_back(it);
           };
           if (k == 0) add_item(0, 1);

@@ -33,6 +33,11 @@ struct Band {
 //   [8..10] -U[i][i+o] / (q-p),  o = 1 .. 3       (upper factor)
 //   [11]    (q-p) / U[i][i]
 constexpr int RSTRIDE = 12;
+// The transposed system (adjoint) uses the same record sizes with the band
+// orientations swapped: radial [0..5] (A - qC)^T[i][i+o]/(q-p), o = -3 .. 2;
+// [6..8] -L[i][i-1..i-3]; [9..10] -U[i][i+1..i+2]/(q-p); [11] (q-p)/U[i][i],
+// where L U is the no-pivot LU of (A - pC)^T.  Vertical: [0..1] -L[c][c-1..c-2];
+// [2] -U[c][c+1]; [3] 1/U[c][c]; [4..7] (D + p'B)^T[c][c+o], o = -2 .. 1.
 // Factors per column of one vertical matrix (D + qB) and the next apply band:
 //   [0]     -L[c][c-1]
 //   [1..2]  -U[c][c+1], -U[c][c+2]
@@ -57,6 +62,8 @@ struct Item {
   long long zoff;     // offset (doubles) of the vertical factors [J][Nz][ZSTRIDE]
   long long r2off;    // offset of the R_2 band table   [M][R2STRIDE]
   long long c02off;   // offset of the C02 band table   [Nz][C02STRIDE]
+  long long roffT;    // transposed radial factors (adjoint), heat only, else -1
+  long long zoffT;    // transposed vertical factors (adjoint), heat only, else -1
 };
 
 struct Shifts {

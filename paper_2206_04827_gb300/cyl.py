@@ -36,7 +36,9 @@ _sig = {
     'cyl_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     'cyl_heat_step': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int]),
     'cyl_heat_adjoint': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
-                                        _vp, _vp]),
+                                        _vp, _vp, _vp, ctypes.c_size_t]),
+    'cyl_heat_adjoint_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
     'cyl_status_string': (ctypes.c_char_p, [ctypes.c_int]),
     'cyl_sync': (ctypes.c_int, [_vp]),
     'cyl_plan_shifts': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -141,12 +143,26 @@ class Plan:
                                   int(nsteps), _ptr(ckpt, 'ckpt', need), int(ckpt_every)), 'cyl_heat_step')
         return T
 
+    def adjoint_workspace_bytes(self, nsteps, ckpt_every, need_alpha):
+        nb = ctypes.c_size_t()
+        _check(_lib.cyl_heat_adjoint_workspace(self._h, int(nsteps), int(ckpt_every), int(bool(need_alpha)),
+                                               ctypes.byref(nb)), 'cyl_heat_adjoint_workspace')
+        return nb.value
+
     def heat_adjoint(self, T0, g, nsteps, dL_dTN, dL_dT0, dL_dg=None, dL_dalpha=None, g_step_stride=0,
-                     ckpt_every=1):
+                     ckpt_every=1, workspace=None):
+        """Reverse-mode gradients of the BDF1 run (see include/cyl.h: cyl_heat_adjoint).
+        The workspace tensor is allocated here (torch) when not given."""
+        nbytes = self.adjoint_workspace_bytes(nsteps, ckpt_every, dL_dalpha is not None)
+        if nbytes and workspace is None:
+            import torch
+            workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=dL_dT0.device)
         _check(_lib.cyl_heat_adjoint(self._h, _ptr(T0, 'T0', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
                                      int(nsteps), int(ckpt_every), _ptr(dL_dTN, 'dL_dTN', self.N),
                                      _ptr(dL_dT0, 'dL_dT0', self.N), _ptr(dL_dg, 'dL_dg', self.N),
-                                     _ptr(dL_dalpha, 'dL_dalpha', 1)), 'cyl_heat_adjoint')
+                                     _ptr(dL_dalpha, 'dL_dalpha', 1),
+                                     _ptr(workspace, 'workspace', (nbytes + 7) // 8) if nbytes else None,
+                                     ctypes.c_size_t(nbytes)), 'cyl_heat_adjoint')
         return dL_dT0
 
     def sync(self):
