@@ -164,6 +164,56 @@ cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
 cyl_status cyl_heat_adjoint_workspace(cyl_plan_t plan, int nsteps, int ckpt_every, int need_alpha,
                                       size_t *bytes);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent cylinders (not in the paper: many problems of
+ * uneven grids and every Fourier mode of each in one persistent launch).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * cyl_plan_batch -- one plan for nprob independent heat problems on grids
+ * n_r[i] x n_z[i] x n_theta[i] (each 4 <= n_r, n_z <= 256, n_theta even >= 2),
+ * diffusivities alpha[i] > 0, one step dt > 0 and one ADI tolerance.  flags:
+ * CYL_WITH_HEAT (required), optionally CYL_BOTH_PARITIES.  The per-problem
+ * host plans are built in parallel threads.  The batch arrays are the
+ * problems' [p][m][n] coefficient arrays concatenated in problem order
+ * (offsets from cyl_batch_layout).  Every (problem, wavenumber, parity) work
+ * item goes into a queue sorted by work, largest first; items whose
+ * max(radial, vertical) block size exceeds a threshold run one per CTA, the
+ * others run G per CTA (thread groups with named barriers); the two classes
+ * are two persistent launches on two streams.  Allocates; not for use inside
+ * stream capture.
+ */
+cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int *n_z,
+                          const int *n_theta, const double *alpha, double dt, double adi_tol,
+                          unsigned flags, void *stream);
+
+/* Number of problems and nprob + 1 prefix offsets (in doubles) of each
+ * problem's array inside the batch arrays (host output; either may be NULL). */
+cyl_status cyl_batch_layout(cyl_plan_t plan, int *nprob, long long *offsets);
+
+/*
+ * cyl_heat_step_batch -- nsteps BDF1 steps of every problem of the batch
+ * (per problem exactly the arithmetic of cyl_heat_step).  T: device batch
+ * array, in/out; g: device batch array of forcings constant in time, or NULL.
+ * No allocation, no host synchronisation: capturable in a CUDA graph.
+ */
+cyl_status cyl_heat_step_batch(cyl_plan_t plan, double *T, const double *g, int nsteps);
+
+/* Launch configuration of a batch plan: threshold on max(M, Nz) between the
+ * one-item-per-CTA class and the G-items-per-CTA class, and G in {1, 2, 4}.
+ * Setting it reallocates the plan's work areas (not during capture). */
+cyl_status cyl_batch_set_config(cyl_plan_t plan, int threshold, int groups);
+cyl_status cyl_batch_get_config(cyl_plan_t plan, int *threshold, int *groups, int *items_per_class);
+
+/*
+ * cyl_batch_autotune -- time every candidate configuration (thresholds
+ * 0/31/47/63/95 x G = 1/2/4) for nsteps steps on copies of the caller's T and
+ * g, keep the fastest and return its time per call in *best_ms (nullable).
+ * T is not modified.  Allocates a temporary batch array; host-synchronising.
+ */
+cyl_status cyl_batch_autotune(cyl_plan_t plan, const double *T, const double *g, int nsteps,
+                              double *best_ms);
+
 /*
  * cyl_sync -- wait for every call queued on the plan's stream, then report
  * device-side failures of those calls: CYL_ETIMEOUT when a bounded wait inside

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cyl.h"
@@ -31,6 +32,22 @@ struct cyl_plan_s {
   double *d_gwork = nullptr;
   double *d_W[6] = {};          // Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i
   double *d_tmp[3] = {};        // N-element scratch arrays
+  // batch plans (cyl_plan_batch): several problems, two persistent launch classes
+  bool is_batch = false;
+  int nprob = 0;
+  std::vector<long long> offsets;   // prefix offsets (doubles) of each problem's arrays
+  std::vector<Item> bitems;         // all items, largest first
+  struct BatchClass {
+    Item *d_items = nullptr;
+    int nitems = 0, G = 1, threads = 128, blocks = 0, ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
+    size_t smem = 0;
+    long long gwork_per_item = 0;
+    double *d_gwork = nullptr;
+    int *d_queue = nullptr;
+  } bc[2];
+  int threshold = 0;                // items with max(M, Nz) > threshold go to class 0
+  cudaStream_t aux = nullptr;       // second stream for the concurrent class
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *d_err = nullptr;         // device status word written by bounded waits
   double *d_apart = nullptr;    // per-item partial sums of the alpha gradient
   size_t N = 0;
@@ -49,7 +66,20 @@ cudaError_t upload(T **dst, const T *src, size_t count) {
   return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+void free_batch(cyl_plan_s *P) {
+  for (auto &c : P->bc) {
+    cudaFree(c.d_items);
+    cudaFree(c.d_gwork);
+    cudaFree(c.d_queue);
+    c = cyl_plan_s::BatchClass();
+  }
+}
+
 void free_device(cyl_plan_s *P) {
+  free_batch(P);
+  if (P->aux) cudaStreamDestroy(P->aux);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   cudaFree(P->d_fac);
   for (auto &p : P->d_items) cudaFree(p);
   cudaFree(P->d_gwork);
@@ -138,6 +168,123 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
+constexpr int kBatchThreads = 128;
+
+// Split a batch's items into two launch classes (threshold on max(M, Nz)) and
+// build their device tables and work areas.  Pairs of Re/Im slices whose
+// shared-memory footprint exceeds a group's budget are split into two items.
+cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
+  free_batch(P);
+  P->threshold = threshold;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  for (int cls = 0; cls < 2; ++cls) {
+    auto &C = P->bc[cls];
+    C.G = cls == 0 ? 1 : G_small;
+    const size_t budget = kSmemLimit / C.G / sizeof(double) - 32;   // doubles per group
+    std::vector<Item> cand;
+    int cM = 0, cNz = 0, cRows = 0, cW1 = 0;
+    for (const Item &it0 : P->bitems) {
+      const bool big = std::max(it0.M, it0.Nz) > threshold;
+      if ((cls == 0) != big) continue;
+      cand.push_back(it0);
+      cM = std::max(cM, it0.M);
+      cNz = std::max(cNz, it0.Nz);
+      cRows = std::max(cRows, it0.Mfull);
+      cW1 = std::max(cW1, it0.Nzfull);
+    }
+    std::vector<Item> items;
+    if (!cand.empty()) {
+      // widest row the group's slice can hold next to the double-buffered tables
+      const long long bands = 2LL * (cM * cyl::RSTRIDE + cNz * cyl::ZSTRIDE);
+      const long long ldmax = ((long long)budget - bands) / cRows;
+      if (ldmax < (cW1 | 1)) return CYL_EINVAL;
+      const int chains_max = 4 * (kBatchThreads / C.G);
+      for (const Item &it0 : cand) {
+        const bool pair_ok = it0.nsl == 2 && ((2 * it0.Nzfull) | 1) <= ldmax &&
+                             2 * std::max(it0.M, it0.Nz) <= chains_max;
+        if (it0.nsl == 2 && !pair_ok) {
+          Item a1 = it0, a2 = it0;
+          a1.nsl = a2.nsl = 1;
+          a2.s0 = it0.s0 + 1;
+          items.push_back(a1);
+          items.push_back(a2);
+        } else {
+          items.push_back(it0);
+        }
+      }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+      return (double)x.J * x.M * x.Nz * x.nsl > (double)y.J * y.M * y.Nz * y.nsl;
+    });
+    C.nitems = (int)items.size();
+    if (C.nitems == 0) continue;
+    for (const Item &it : items) {
+      C.maxM = std::max(C.maxM, it.M);
+      C.maxNz = std::max(C.maxNz, it.Nz);
+      C.smem_rows = std::max(C.smem_rows, it.Mfull);
+      C.ld = std::max(C.ld, it.nsl * it.Nzfull);
+    }
+    C.ld |= 1;
+    C.threads = kBatchThreads;
+    C.smem = cyl::batch_smem_bytes(C.G, C.ld, C.smem_rows, C.maxM, C.maxNz);
+    if (C.smem > kSmemLimit) return CYL_EINVAL;
+    C.blocks = std::min(C.nitems, sms * std::max(1, (int)(kSmemLimit / std::max<size_t>(C.smem, 1))));
+    C.blocks = std::max(1, std::min(C.blocks, 4 * sms));
+    C.gwork_per_item = ((long long)C.maxM * C.ld + 31) / 32 * 32;
+    cudaError_t e = upload(&C.d_items, items.data(), items.size());
+    if (e == cudaSuccess)
+      e = cudaMalloc((void **)&C.d_gwork, (size_t)C.gwork_per_item * C.blocks * C.G * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&C.d_queue, sizeof(int));
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return CYL_OK;
+}
+
+cyl_status run_batch(cyl_plan_s *P, double *T, const double *g, int nsteps) {
+  bool two = P->bc[0].nitems > 0 && P->bc[1].nitems > 0;
+  cudaError_t e = cudaSuccess;
+  if (two) {
+    e = cudaEventRecord(P->ev_fork, P->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  for (int cls = 0; cls < 2; ++cls) {
+    auto &C = P->bc[cls];
+    if (C.nitems == 0) continue;
+    cyl::AdiArgs a{};
+    a.items = C.d_items;
+    a.nitems = C.nitems;
+    a.fac = P->d_fac;
+    a.Xin = T;
+    a.Xout = T;
+    a.G = g;
+    a.kappa = P->hp.dt;
+    a.gstride = 0;
+    a.nsteps = nsteps;
+    a.ckpt_every = 1;
+    a.zero_other = (P->hp.flags & CYL_BOTH_PARITIES) ? 0 : 1;
+    a.gwork = C.d_gwork;
+    a.gwork_per_item = C.gwork_per_item;
+    a.use_smem = 1;
+    a.ld = C.ld;
+    a.smem_rows = C.smem_rows;
+    a.maxM = C.maxM;
+    a.maxNz = C.maxNz;
+    a.err = P->d_err;
+    a.group_doubles = (long long)cyl::batch_group_doubles(C.ld, C.smem_rows, C.maxM, C.maxNz);
+    if (a.group_doubles % 32 != 0 || (size_t)a.group_doubles * C.G * sizeof(double) > C.smem) return CYL_EINVAL;
+    cudaStream_t st = (two && cls == 1) ? P->aux : P->st;
+    e = cyl::launch_batch(a, C.d_queue, C.G, C.threads, C.blocks, C.smem, st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  if (two) {
+    e = cudaEventRecord(P->ev_join, P->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->st, P->ev_join, 0);
+  }
+  return from_cuda(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -199,10 +346,13 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
     int thr = 32;
     for (const Item &it : h.kind[kind].items) thr = std::max(thr, std::max(it.nsl * it.Nz, it.nsl * it.M));
     P->threads[kind] = (thr + 31) / 32 * 32;
-    const bool fits = !(flags & CYL_FORCE_GLOBAL) &&
-                      cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, true) <= kSmemLimit;
-    P->use_smem[kind] = fits ? 1 : 0;
-    P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, fits);
+    int level = 0;
+    if (!(flags & CYL_FORCE_GLOBAL)) {
+      if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 2) <= kSmemLimit) level = 2;
+      else if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 1) <= kSmemLimit) level = 1;
+    }
+    P->use_smem[kind] = level;
+    P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, level);
   }
   if (P->threads[0] > 512 || P->threads[1] > 512) {
     delete P;
@@ -224,7 +374,7 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_apart, std::max(1, P->nitems[1]) * sizeof(double));
-  if (e == cudaSuccess && !(P->use_smem[0] && P->use_smem[1])) {
+  if (e == cudaSuccess && !(P->use_smem[0] == 2 && P->use_smem[1] == 2)) {
     P->gwork_per_item = ((long long)P->smem_rows * P->ld + (long long)P->maxM * P->ld + 31) / 32 * 32;
     const int maxItems = std::max(P->nitems[0], P->nitems[1]);
     e = cudaMalloc((void **)&P->d_gwork, (size_t)P->gwork_per_item * maxItems * sizeof(double));
@@ -248,19 +398,19 @@ cyl_status cyl_destroy(cyl_plan_t P) {
 
 cyl_status cyl_vals2coeffs(cyl_plan_t P, const double *vals, double *coeffs) {
   if (!P || !vals || !coeffs) return CYL_EINVAL;
-  if (P->host_only) return CYL_ESTATE;
+  if (P->host_only || P->is_batch) return CYL_ESTATE;
   return vals2coeffs_impl(P, vals, coeffs);
 }
 
 cyl_status cyl_coeffs2vals(cyl_plan_t P, const double *coeffs, double *vals) {
   if (!P || !vals || !coeffs) return CYL_EINVAL;
-  if (P->host_only) return CYL_ESTATE;
+  if (P->host_only || P->is_batch) return CYL_ESTATE;
   return coeffs2vals_impl(P, coeffs, vals);
 }
 
 cyl_status cyl_poisson(cyl_plan_t P, const double *f, double *u, int space) {
   if (!P || !f || !u || (space != CYL_VALUES && space != CYL_COEFFS)) return CYL_EINVAL;
-  if (P->host_only || !P->hp.kind[0].built) return CYL_ESTATE;
+  if (P->host_only || P->is_batch || !P->hp.kind[0].built) return CYL_ESTATE;
   if (space == CYL_COEFFS) return run_adi(P, 0, f, u, nullptr, 0.0, 0, 1, nullptr, 1);
   cyl_status s = vals2coeffs_impl(P, f, P->d_tmp[2]);
   if (s != CYL_OK) return s;
@@ -272,6 +422,7 @@ cyl_status cyl_poisson(cyl_plan_t P, const double *f, double *u, int space) {
 cyl_status cyl_heat_step(cyl_plan_t P, double *T, const double *g, long long g_step_stride, int nsteps,
                          double *ckpt, int ckpt_every) {
   if (!P || !T || nsteps < 0 || g_step_stride < 0) return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
   if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
   if (ckpt && ckpt_every < 1) return CYL_EINVAL;
   if (P->host_only || !P->hp.kind[1].built) return CYL_ESTATE;
@@ -303,7 +454,7 @@ cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, lon
   if (!P || !dL_dTN || !dL_dT0 || nsteps < 0 || ckpt_every < 1 || g_step_stride < 0) return CYL_EINVAL;
   if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
   if (dL_dalpha && !T0) return CYL_EINVAL;
-  if (P->host_only || !P->hp.kind[1].built) return CYL_ESTATE;
+  if (P->host_only || P->is_batch || !P->hp.kind[1].built) return CYL_ESTATE;
   const size_t need = adjoint_workspace_doubles(P, nsteps, ckpt_every, dL_dalpha != nullptr);
   if (need && (!workspace || workspace_bytes < need * sizeof(double))) return CYL_EINVAL;
   const size_t N = P->N;
@@ -377,6 +528,7 @@ cyl_status cyl_sync(cyl_plan_t P) {
 
 cyl_status cyl_grid(cyl_plan_t P, double *r, double *z, double *theta) {
   if (!P) return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
   const HostPlan &h = P->hp;
   const double pi = 3.14159265358979323846;
   if (r)
@@ -392,6 +544,7 @@ cyl_status cyl_plan_shifts(cyl_plan_t P, int which, int k, int parity, int *J, d
                            double *p_shift, double *q_shift) {
   if (!P || !J || which < 0 || which > 1 || k < 0 || k > P->hp.p / 2 || parity < 0 || parity > 1)
     return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
   const auto &KT = P->hp.kind[which];
   if (!KT.built) return CYL_ESTATE;
   const cyl::Shifts &S = KT.shifts[k * 2 + parity];
@@ -409,6 +562,7 @@ cyl_status cyl_plan_operator(cyl_plan_t P, int op, int which, int k, int parity,
   if (!P || !dim || op < 0 || op > 3 || which < 0 || which > 1 || parity < 0 || parity > 1 || k < 0 ||
       k > P->hp.p / 2)
     return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
   const HostPlan &h = P->hp;
   if (which == 1 && !(h.alpha > 0 && h.dt > 0)) return CYL_ESTATE;
   const double ka = which == 1 ? h.alpha * h.dt : 1.0;
@@ -433,6 +587,160 @@ cyl_status cyl_plan_operator(cyl_plan_t P, int op, int which, int k, int parity,
     for (int i = 0; i < B.n; ++i)
       for (int j = 0; j < B.n; ++j) out[(size_t)i * B.n + j] = B.get(i, j);
   return CYL_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int *n_z, const int *n_theta,
+                          const double *alpha, double dt, double adi_tol, unsigned flags, void *stream) {
+  if (!plan) return CYL_EINVAL;
+  *plan = nullptr;
+  if (nprob < 1 || !n_r || !n_z || !n_theta || !alpha || !(dt > 0.0)) return CYL_EINVAL;
+  if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
+  if (!(flags & CYL_WITH_HEAT) || (flags & ~(unsigned)(CYL_WITH_HEAT | CYL_BOTH_PARITIES))) return CYL_EINVAL;
+  for (int i = 0; i < nprob; ++i)
+    if (n_r[i] < 4 || n_z[i] < 4 || n_theta[i] < 2 || (n_theta[i] & 1) || !(alpha[i] > 0.0) ||
+        n_r[i] > 256 || n_z[i] > 256)
+      return CYL_EINVAL;
+  cyl_plan_s *P = new (std::nothrow) cyl_plan_s();
+  if (!P) return CYL_ENOMEM;
+  P->is_batch = true;
+  P->nprob = nprob;
+  P->st = (cudaStream_t)stream;
+  // host plans in parallel (independent problems)
+  std::vector<HostPlan> hps(nprob);
+  std::vector<std::string> errs(nprob);
+  const int nth = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t)
+    pool.emplace_back([&, t]() {
+      for (int i = t; i < nprob; i += nth) {
+        try {
+          errs[i] = cyl::build_host_plan(hps[i], n_r[i], n_z[i], n_theta[i], alpha[i], dt, adi_tol,
+                                         (flags & CYL_BOTH_PARITIES) | CYL_WITH_HEAT);
+        } catch (...) {
+          errs[i] = "host plan failed";
+        }
+      }
+    });
+  for (auto &th : pool) th.join();
+  for (int i = 0; i < nprob; ++i)
+    if (!errs[i].empty()) {
+      delete P;
+      return CYL_EINVAL;
+    }
+  // merge factor tables and items
+  P->offsets.assign(nprob + 1, 0);
+  size_t ftotal = 0;
+  for (int i = 0; i < nprob; ++i) {
+    P->offsets[i + 1] = P->offsets[i] + (long long)n_r[i] * n_z[i] * n_theta[i];
+    ftotal += hps[i].factors.size();
+  }
+  P->N = (size_t)P->offsets[nprob];
+  std::vector<double> fac;
+  fac.reserve(ftotal);
+  for (int i = 0; i < nprob; ++i) {
+    const long long base = (long long)fac.size();
+    fac.insert(fac.end(), hps[i].factors.begin(), hps[i].factors.end());
+    for (Item it : hps[i].kind[1].items) {
+      it.roff += base; it.zoff += base; it.r2off += base; it.c02off += base;
+      if (it.roffT >= 0) it.roffT += base;
+      if (it.zoffT >= 0) it.zoffT += base;
+      it.xoff = P->offsets[i];
+      P->bitems.push_back(it);
+    }
+  }
+  P->hp.flags = flags;
+  P->hp.dt = dt;
+  P->hp.tol = adi_tol;
+  P->hp.kind[1].built = true;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e == cudaSuccess) e = upload(&P->d_fac, fac.data(), fac.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
+  cyl_status s = from_cuda(e);
+  if (s == CYL_OK) s = configure_batch(P, 63, 4);
+  if (s != CYL_OK) {
+    free_device(P);
+    delete P;
+    cudaGetLastError();
+    return s;
+  }
+  *plan = P;
+  return CYL_OK;
+}
+
+cyl_status cyl_batch_layout(cyl_plan_t P, int *nprob, long long *offsets) {
+  if (!P || !P->is_batch) return CYL_EINVAL;
+  if (nprob) *nprob = P->nprob;
+  if (offsets) std::memcpy(offsets, P->offsets.data(), (P->nprob + 1) * sizeof(long long));
+  return CYL_OK;
+}
+
+cyl_status cyl_heat_step_batch(cyl_plan_t P, double *T, const double *g, int nsteps) {
+  if (!P || !T || nsteps < 0) return CYL_EINVAL;
+  if (!P->is_batch) return CYL_ESTATE;
+  if (nsteps == 0) return CYL_OK;
+  return run_batch(P, T, g, nsteps);
+}
+
+cyl_status cyl_batch_set_config(cyl_plan_t P, int threshold, int groups) {
+  if (!P || !P->is_batch || (groups != 1 && groups != 2 && groups != 4) || threshold < 0) return CYL_EINVAL;
+  return configure_batch(P, threshold, groups);
+}
+
+cyl_status cyl_batch_get_config(cyl_plan_t P, int *threshold, int *groups, int *items_per_class) {
+  if (!P || !P->is_batch) return CYL_EINVAL;
+  if (threshold) *threshold = P->threshold;
+  if (groups) *groups = P->bc[1].G;
+  if (items_per_class) {
+    items_per_class[0] = P->bc[0].nitems;
+    items_per_class[1] = P->bc[1].nitems;
+  }
+  return CYL_OK;
+}
+
+cyl_status cyl_batch_autotune(cyl_plan_t P, const double *T, const double *g, int nsteps, double *best_ms) {
+  if (!P || !P->is_batch || !T || nsteps < 1) return CYL_EINVAL;
+  double *work = nullptr;
+  cudaError_t e = cudaMalloc((void **)&work, P->N * sizeof(double));
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int thresholds[] = {0, 31, 47, 63, 95};
+  const int groups[] = {1, 2, 4};
+  float best = 1e30f;
+  int bt = 63, bg = 4;
+  cyl_status s = CYL_OK;
+  for (int th : thresholds)
+    for (int G : groups) {
+      if (th == 0 && G != 1) continue;
+      s = configure_batch(P, th, G);
+      if (s != CYL_OK) { s = CYL_OK; continue; }
+      float ms = 0;
+      for (int rep = 0; rep < 2 && s == CYL_OK; ++rep) {
+        cudaMemcpyAsync(work, T, P->N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+        cudaEventRecord(e0, P->st);
+        s = run_batch(P, work, g, nsteps);
+        cudaEventRecord(e1, P->st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (s != CYL_OK) break;
+      if (ms < best) { best = ms; bt = th; bg = G; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(work);
+  if (s != CYL_OK) return s;
+  if (best_ms) *best_ms = best;
+  return configure_batch(P, bt, bg);
 }
 
 }  // extern "C"

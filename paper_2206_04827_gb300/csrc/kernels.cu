@@ -23,9 +23,10 @@
 
 namespace cyl {
 
-size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem) {
+size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level) {
   size_t d = 2 * ((size_t)maxM * RSTRIDE + (size_t)maxNz * ZSTRIDE);   // double-buffered factor tables
-  if (arrays_in_smem) d += (size_t)smem_rows * ld + (size_t)maxM * ld;
+  if (level >= 1) d += (size_t)smem_rows * ld;                         // iterate S
+  if (level >= 2) d += (size_t)maxM * ld;                              // right side Fa
   return d * sizeof(double);
 }
 
@@ -252,9 +253,20 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
   }
 }
 
+// A group of threads that processes one item: the whole CTA (named barrier 0)
+// or one of G equal slices of it (named barriers 1 .. G).
+struct Grp {
+  int tid, nth, bar;
+  __device__ __forceinline__ void sync() const {
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nth) : "memory");
+  }
+};
+
 // J iterations of Algorithm 1 on one item from X_0 = 0: right side in Fa,
-// result in S.  Factor tables of iteration c (counted over all steps of the
-// launch) arrive in buffer c & 1 by TMA bulk copies issued one iteration ahead.
+// result in S.  Factor tables of iteration c (counted per group over every
+// step and item it processes; c0 = the item's first iteration) arrive in
+// buffer c & 1 by TMA bulk copies issued one iteration ahead.
 struct AdiShared {
   double *RB0, *ZB0;
   int rlen, zlen;
@@ -262,8 +274,9 @@ struct AdiShared {
 };
 
 template <bool TRANS>
-__device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs &a, const Item &it, long long c) {
-  const int jt = (int)(c % it.J), buf = (int)(c & 1);
+__device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs &a, const Item &it, long long c,
+                                             long long c0) {
+  const int jt = (int)((c - c0) % it.J), buf = (int)(c & 1);
   const unsigned rbytes = (unsigned)(it.M * RSTRIDE * sizeof(double));
   const unsigned zbytes = (unsigned)(it.Nz * ZSTRIDE * sizeof(double));
   const long long roff = TRANS ? it.roffT : it.roff, zoff = TRANS ? it.zoffT : it.zoff;
@@ -273,74 +286,61 @@ __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs 
 }
 
 template <bool TRANS>
-__device__ __forceinline__ void adi_iterations(const AdiShared &sh, const AdiArgs &a, const Item &it, double *S,
-                                               double *Fa, long long &c, long long total_it, bool &timed_out) {
-  const int tid = threadIdx.x, M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, ld = a.ld, J = it.J;
+__device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &sh, const AdiArgs &a, const Item &it,
+                                               double *S, const double *Fa, int ldF, long long &c, long long c0,
+                                               long long c_end, bool &timed_out) {
+  const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, ld = a.ld, J = it.J;
   for (int jt = 0; jt < J; ++jt, ++c) {
     const int buf = (int)(c & 1);
-    if (tid == 0 && c + 1 < total_it) {
+    if (gp.tid == 0 && c + 1 < c_end) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tables<TRANS>(sh, a, it, c + 1);
+      issue_tables<TRANS>(sh, a, it, c + 1, c0);
     }
     if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1))) timed_out = true;
     const double *RB = sh.RB0 + buf * sh.rlen;
     const double *ZB = sh.ZB0 + buf * sh.zlen;
-    if (tid < W) {
-      if (jt == 0) radial_sweep<true, TRANS>(S + tid, Fa + tid, ld, RB, M);
-      else radial_sweep<false, TRANS>(S + tid, Fa + tid, ld, RB, M);
+    for (int col = gp.tid; col < W; col += gp.nth) {
+      if (jt == 0) radial_sweep<true, TRANS>(S + col, Fa + col, ld, RB, M);
+      else radial_sweep<false, TRANS>(S + col, Fa + col, ld, RB, M);
     }
-    __syncthreads();
-    if (tid < nsl * M) {
-      const int sl = tid / M, aa = tid - sl * M;
+    gp.sync();
+    for (int r = gp.tid; r < nsl * M; r += gp.nth) {
+      const int sl = r / M, aa = r - sl * M;
       if (jt + 1 == J) vertical_sweep<true, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
       else vertical_sweep<false, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
     }
-    __syncthreads();
+    gp.sync();
   }
+  (void)ldF;
 }
 
-template <bool SMEM>
-__device__ __forceinline__ void setup_shared(const AdiArgs &a, AdiShared &sh, double *&S, double *&Fa, double *sm,
-                                             unsigned long long *bar) {
-  sh.rlen = a.maxM * RSTRIDE;
-  sh.zlen = a.maxNz * ZSTRIDE;
-  sh.RB0 = sm;                          // [2][maxM * RSTRIDE]
-  sh.ZB0 = sm + 2 * sh.rlen;            // [2][maxNz * ZSTRIDE]
-  sh.bar = bar;
-  if (SMEM) S = sh.ZB0 + 2 * sh.zlen;
-  else S = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
-  Fa = S + (size_t)a.smem_rows * a.ld;
-  if (threadIdx.x == 0) {
+__device__ __forceinline__ void init_bars(const Grp &gp, unsigned long long *bar) {
+  if (gp.tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
+  gp.sync();
 }
 
-template <bool SMEM>
-__global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
-  extern __shared__ __align__(16) double sm[];
-  __shared__ __align__(8) unsigned long long bar[2];
-  const Item it = a.items[blockIdx.x];
-  const int tid = threadIdx.x, nth = blockDim.x;
+// Every BDF1 step of one item (see adi_kernel): right side, ADI, expansion.
+__device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArgs &a, const Item &it,
+                                                     const AdiShared &sh, double *S, double *Fa, long long &c,
+                                                     bool &timed_out) {
+  const int tid = gp.tid, nth = gp.nth;
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz;
   const int ld = a.ld;
-  const int m = a.m, n = a.n;
+  const int m = it.m, n = it.n;
   const long long slice = (long long)m * n;
-  AdiShared sh;
-  double *S, *Fa;
-  setup_shared<SMEM>(a, sh, S, Fa, sm, bar);
   const double *r2 = a.fac + it.r2off;
   const double *c02 = a.fac + it.c02off;
-  const long long total_it = (long long)a.nsteps * it.J;
-  if (tid == 0) issue_tables<false>(sh, a, it, 0);
-  bool timed_out = false;
-
-  const double *Xsrc = a.Xin;
-  long long c = 0;
+  const long long c0 = c, c_end = c0 + (long long)a.nsteps * it.J;
+  if (tid == 0) issue_tables<false>(sh, a, it, c0, c0);
+  const double *Xsrc = a.Xin + it.xoff;
+  double *Xout = a.Xout + it.xoff;
+  const double *Gbase = a.G ? a.G + it.xoff : nullptr;
   for (int step = 0; step < a.nsteps; ++step) {
-    const double *Gs = a.G ? a.G + (size_t)step * a.gstride : nullptr;
+    const double *Gs = Gbase ? Gbase + (size_t)step * a.gstride : nullptr;
     // Right side of eq. HelmholtzMatEqn, E = trunc(R_2 (X + kappa g) C02^T), in two
     // banded passes: T1 = (X + kappa g) C02^T on the class rows, then E = R_2 T1.
     for (int e = tid; e < it.Mfull * W; e += nth) {
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
       }
       S[ap * ld + cc] = acc;
     }
-    __syncthreads();
+    gp.sync();
     for (int e = tid; e < M * W; e += nth) {
       const int aa = e / W, cc = e - aa * W;
       double acc = 0.0;
@@ -371,26 +371,26 @@ __global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
       }
       Fa[aa * ld + cc] = acc;
     }
-    __syncthreads();
+    gp.sync();
 
-    adi_iterations<false>(sh, a, it, S, Fa, c, total_it, timed_out);
+    adi_iterations<false>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
     const int Wf = nsl * it.Nzfull;
     const bool do_ck = a.ckpt && ((step + 1) % a.ckpt_every == 0);
-    double *ck = do_ck ? a.ckpt + (size_t)((step + 1) / a.ckpt_every) * (size_t)a.p * slice : nullptr;
+    double *ck = do_ck ? a.ckpt + it.xoff + (size_t)((step + 1) / a.ckpt_every) * (size_t)a.p * slice : nullptr;
     for (int e = tid; e < it.Mfull * Wf; e += nth) {
       const int ap = e / Wf, cc = e - ap * Wf;
       const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
       const double *Ys = S + sl * Nz;
-      const bool r0 = ap - 1 >= 0, r1 = ap < M, c0 = b - 1 >= 0, c1 = b < Nz;
+      const bool r0 = ap - 1 >= 0, r1 = ap < M, c0b = b - 1 >= 0, c1 = b < Nz;
       double x = 0.0;
-      if (r0 && c0) x += Ys[(ap - 1) * ld + b - 1];
+      if (r0 && c0b) x += Ys[(ap - 1) * ld + b - 1];
       if (r0 && c1) x -= Ys[(ap - 1) * ld + b];
-      if (r1 && c0) x -= Ys[ap * ld + b - 1];
+      if (r1 && c0b) x -= Ys[ap * ld + b - 1];
       if (r1 && c1) x += Ys[ap * ld + b];
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * ap) * n + it.pz + 2 * b;
-      a.Xout[o] = x;
+      Xout[o] = x;
       if (ck) ck[o] = x;
     }
     if (a.zero_other) {
@@ -399,14 +399,110 @@ __global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
         const int ap = e / Wf, cc = e - ap * Wf;
         const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
         const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(po + 2 * ap) * n + it.pz + 2 * b;
-        a.Xout[o] = 0.0;
+        Xout[o] = 0.0;
         if (ck) ck[o] = 0.0;
       }
     }
-    __syncthreads();
-    Xsrc = a.Xout;
+    gp.sync();
+    Xsrc = Xout;
+  }
+}
+
+// One CTA per item.  S_SMEM / F_SMEM place the item's iterate (S) and right
+// side (Fa) in shared memory, else in the per-item global work area.
+template <bool S_SMEM, bool F_SMEM>
+__global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  const Item it = a.items[blockIdx.x];
+  const Grp gp{(int)threadIdx.x, (int)blockDim.x, 0};
+  AdiShared sh;
+  sh.rlen = a.maxM * RSTRIDE;
+  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.RB0 = sm;
+  sh.ZB0 = sm + 2 * sh.rlen;
+  sh.bar = bar;
+  double *smem_next = sh.ZB0 + 2 * sh.zlen;
+  double *gw = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
+  double *S = S_SMEM ? smem_next : gw;
+  if (S_SMEM) smem_next += (size_t)a.smem_rows * a.ld;
+  double *Fa = F_SMEM ? smem_next : gw + (S_SMEM ? 0 : (size_t)a.smem_rows * a.ld);
+  init_bars(gp, bar);
+  bool timed_out = false;
+  long long c = 0;
+  process_item_forward(gp, a, it, sh, S, Fa, c, timed_out);
+  if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+// Persistent batch kernel: the CTA is split into G groups of blockDim.x / G
+// threads; each group pulls items (largest first) from a queue and runs every
+// step of each.  S lives in the group's shared-memory slice, Fa in the
+// group's global work area.
+template <int G>
+__global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int *queue) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) unsigned long long bar[2 * G];
+  __shared__ int next_item[G];
+  const int gsize = blockDim.x / G, g = threadIdx.x / gsize;
+  const Grp gp{(int)threadIdx.x - g * gsize, gsize, G == 1 ? 0 : 1 + g};
+  // every group's slice starts on a 256-byte boundary (TMA destinations and
+  // double2 loads of the factor tables need 16-byte alignment)
+  double *base = sm + (size_t)g * (size_t)a.group_doubles;
+  AdiShared sh;
+  sh.rlen = a.maxM * RSTRIDE;
+  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.RB0 = base;
+  sh.ZB0 = base + 2 * sh.rlen;
+  sh.bar = bar + 2 * g;
+  double *S = sh.ZB0 + 2 * sh.zlen;
+  double *Fa = a.gwork + ((size_t)blockIdx.x * G + g) * a.gwork_per_item;
+  init_bars(gp, sh.bar);
+  bool timed_out = false;
+  long long c = 0;
+  for (;;) {
+    if (gp.tid == 0) next_item[g] = atomicAdd(queue, 1);
+    gp.sync();
+    const int idx = next_item[g];
+    gp.sync();
+    if (idx >= a.nitems) break;
+    const Item it = a.items[idx];
+    process_item_forward(gp, a, it, sh, S, Fa, c, timed_out);
   }
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz) {
+  const size_t d = (size_t)2 * (maxM * RSTRIDE + maxNz * ZSTRIDE) + (size_t)smem_rows * ld;
+  return (d + 31) / 32 * 32;
+}
+
+size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz) {
+  return batch_group_doubles(ld, smem_rows, maxM, maxNz) * G * sizeof(double);
+}
+
+cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int blocks, size_t smem,
+                         cudaStream_t st) {
+  if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  switch (G) {
+    case 1:
+      e = cudaFuncSetAttribute(adi_batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) adi_batch_kernel<1><<<blocks, threads, smem, st>>>(a, queue);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(adi_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) adi_batch_kernel<2><<<blocks, threads, smem, st>>>(a, queue);
+      break;
+    case 4:
+      e = cudaFuncSetAttribute(adi_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) adi_batch_kernel<4><<<blocks, threads, smem, st>>>(a, queue);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 // Adjoint of the BDF1 steps n = n_hi-1 .. n_lo for one item (the transpose of
@@ -425,16 +521,23 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
   const int tid = threadIdx.x, nth = blockDim.x;
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, Wf = nsl * it.Nzfull;
   const int ld = a.ld;
-  const int m = a.m, n = a.n;
+  const int m = it.m, n = it.n;
   const long long slice = (long long)m * n, Ntot = (long long)a.p * slice;
   AdiShared sh;
-  double *S, *Fa;
-  setup_shared<SMEM>(a, sh, S, Fa, sm, bar);
+  sh.rlen = a.maxM * RSTRIDE;
+  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.RB0 = sm;
+  sh.ZB0 = sm + 2 * sh.rlen;
+  sh.bar = bar;
+  double *S = SMEM ? sh.ZB0 + 2 * sh.zlen : a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
+  double *Fa = S + (size_t)a.smem_rows * ld;
+  const Grp gp{tid, nth, 0};
+  init_bars(gp, bar);
   const double *r2 = a.fac + it.r2off;
   const double *c02 = a.fac + it.c02off;
   const int nst = g.n_hi - g.n_lo;
   const long long total_it = (long long)nst * it.J;
-  if (tid == 0) issue_tables<true>(sh, a, it, 0);
+  if (tid == 0) issue_tables<true>(sh, a, it, 0, 0);
   bool timed_out = false;
   double apart = 0.0;
   double *lam = g.lam;
@@ -448,7 +551,7 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
       Fa[aa * ld + cc] = lam[o] - lam[o + 2] - lam[o + 2 * n] + lam[o + 2 * n + 2];
     }
     __syncthreads();
-    adi_iterations<true>(sh, a, it, S, Fa, c, total_it, timed_out);
+    adi_iterations<true>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
     // T1 = Lambda C02 on nsl * Nzfull columns: T1[a][b'] = sum_t Lambda[a][b' - t] C02[b' - t][t]
     for (int e = tid; e < M * Wf; e += nth) {
       const int aa = e / Wf, cc = e - aa * Wf;
@@ -528,7 +631,7 @@ cudaError_t launch_sum_partials(const double *part, int n, double scale, double 
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || g.n_hi <= g.n_lo) return cudaSuccess;
   cudaError_t e;
-  if (a.use_smem) {
+  if (a.use_smem == 2) {
     e = cudaFuncSetAttribute(adi_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     adi_adjoint_kernel<true><<<a.nitems, threads, smem, st>>>(a, g);
@@ -543,14 +646,18 @@ cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
   cudaError_t e;
-  if (a.use_smem) {
-    e = cudaFuncSetAttribute(adi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (a.use_smem == 2) {
+    e = cudaFuncSetAttribute(adi_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    adi_kernel<true><<<a.nitems, threads, smem, st>>>(a);
+    adi_kernel<true, true><<<a.nitems, threads, smem, st>>>(a);
+  } else if (a.use_smem == 1) {
+    e = cudaFuncSetAttribute(adi_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_kernel<true, false><<<a.nitems, threads, smem, st>>>(a);
   } else {
-    e = cudaFuncSetAttribute(adi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(adi_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    adi_kernel<false><<<a.nitems, threads, smem, st>>>(a);
+    adi_kernel<false, false><<<a.nitems, threads, smem, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -25,11 +25,12 @@ struct AdiArgs {
   int transpose;           // 0: forward solve, 1: transposed (adjoint) solve
   double *gwork;           // global work arrays when the item does not fit in shared memory
   long long gwork_per_item;
-  int use_smem;
+  int use_smem;            // 2: S and Fa in shared memory, 1: S only, 0: neither
   int ld;                  // leading dimension of the work arrays (odd)
   int smem_rows;           // rows of the S array (max Mfull)
   int maxM, maxNz;         // band table sizes in shared memory
   int *err;                // device status word (CYL_ERR_TIMEOUT on a bounded-wait timeout)
+  long long group_doubles; // batch kernel: shared-memory slice per thread group (multiple of 32)
 };
 
 constexpr int CYL_ERR_TIMEOUT = 4;
@@ -50,7 +51,11 @@ struct AdjointArgs {
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st);
 
-size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, bool arrays_in_smem);
+size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level);
+size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz);
+size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz);
+cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int blocks, size_t smem,
+                         cudaStream_t st);
 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st);
 

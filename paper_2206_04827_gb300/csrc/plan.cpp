@@ -531,6 +531,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             it.M = M; it.Mfull = hp.Mfull[pr]; it.Nz = Nz; it.Nzfull = hp.Nfull[pz];
             it.J = S.J; it.roff = roff; it.zoff = zoff; it.r2off = r2off[pr]; it.c02off = c02off[pz];
             it.roffT = roffT; it.zoffT = zoffT;
+            it.m = m; it.n = n; it.xoff = 0;
             KT.items.push_back(it);
           };
           if (k == 0) add_item(0, 1);

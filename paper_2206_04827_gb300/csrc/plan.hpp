@@ -57,7 +57,8 @@ struct Item {
   int M, Mfull;       // unknown rows (class rows < m-2), class rows < m
   int Nz, Nzfull;     // unknown cols (class cols < n-2), class cols < n
   int J;              // ADI iterations
-  int pad0;
+  int m, n;           // grid of the item's problem (n_r, n_z)
+  long long xoff;     // offset (doubles) of the problem's arrays in a batch (0 for one problem)
   long long roff;     // offset (doubles) of the radial factors  [J][M][RSTRIDE]
   long long zoff;     // offset (doubles) of the vertical factors [J][Nz][ZSTRIDE]
   long long r2off;    // offset of the R_2 band table   [M][R2STRIDE]

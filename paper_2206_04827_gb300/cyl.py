@@ -46,6 +46,16 @@ _sig = {
     'cyl_plan_operator': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), _c_double_p]),
     'cyl_grid': (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
+    'cyl_plan_batch': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_uint, _vp]),
+    'cyl_batch_layout': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+    'cyl_heat_step_batch': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    'cyl_batch_set_config': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    'cyl_batch_get_config': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int)]),
+    'cyl_batch_autotune': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
     'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
 }
@@ -195,6 +205,66 @@ class Plan:
         buf = (ctypes.c_double * (d.value * d.value))()
         _check(_lib.cyl_plan_operator(self._h, op, which, k, parity, ctypes.byref(d), buf), 'cyl_plan_operator')
         return np.array(buf).reshape(d.value, d.value)
+
+
+class BatchPlan:
+    """Owner of a batch plan (see include/cyl.h: cyl_plan_batch)."""
+
+    def __init__(self, n_r, n_z, n_theta, alpha, dt, adi_tol=1e-14, both_parities=False, stream=None):
+        k = len(n_r)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        ia = lambda v: (ctypes.c_int * k)(*[int(x) for x in v])
+        self._h = _vp()
+        _check(_lib.cyl_plan_batch(ctypes.byref(self._h), k, ia(n_r), ia(n_z), ia(n_theta),
+                                   (ctypes.c_double * k)(*[float(a) for a in alpha]), float(dt), float(adi_tol),
+                                   WITH_HEAT | (BOTH_PARITIES if both_parities else 0), _vp(stream)),
+               'cyl_plan_batch')
+        offs = (ctypes.c_longlong * (k + 1))()
+        _check(_lib.cyl_batch_layout(self._h, None, offs), 'cyl_batch_layout')
+        self.offsets = [int(o) for o in offs]
+        self.shapes = [(int(p), int(m), int(n)) for m, n, p in zip(n_r, n_z, n_theta)]
+        self.N = self.offsets[-1]
+
+    def close(self):
+        if self._h:
+            _lib.cyl_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def heat_step(self, T, g=None, nsteps=1):
+        _check(_lib.cyl_heat_step_batch(self._h, _ptr(T, 'T', self.N), _ptr(g, 'g', self.N), int(nsteps)),
+               'cyl_heat_step_batch')
+        return T
+
+    def set_config(self, threshold, groups):
+        _check(_lib.cyl_batch_set_config(self._h, int(threshold), int(groups)), 'cyl_batch_set_config')
+
+    def config(self):
+        t, g = ctypes.c_int(), ctypes.c_int()
+        ipc = (ctypes.c_int * 2)()
+        _check(_lib.cyl_batch_get_config(self._h, ctypes.byref(t), ctypes.byref(g), ipc), 'cyl_batch_get_config')
+        return t.value, g.value, (ipc[0], ipc[1])
+
+    def autotune(self, T, g=None, nsteps=1):
+        ms = ctypes.c_double()
+        _check(_lib.cyl_batch_autotune(self._h, _ptr(T, 'T', self.N), _ptr(g, 'g', self.N), int(nsteps),
+                                       ctypes.byref(ms)), 'cyl_batch_autotune')
+        return ms.value
+
+    def sync(self):
+        _check(_lib.cyl_sync(self._h), 'cyl_sync')
+
+    def view(self, T, i):
+        """Problem i's [p][m][n] view of a batch array."""
+        p, m, n = self.shapes[i]
+        return T[self.offsets[i]:self.offsets[i + 1]].view(p, m, n)
 
 
 def exported_symbols():
