@@ -1,11 +1,20 @@
-"""Benchmark: FP64 unknowns*steps/s of the CCF cylinder heat solver on one GB300.
+"""Benchmark: FP64 unknowns*steps/s of the CCF cylinder solver on one GB300.
 
-Workload (one bench step): the 128^3 heat problem -- n_r = n_z = n_theta = 128,
-alpha = 1, dt = 1e-3, 100 implicit BDF1 steps, T0 = 8 Bessel x sine
-eigenmodes with seeded N(0,1) amplitudes, g = seeded smooth CCF coefficients
-N(0,1) * 1.25^-(i+j+|k|).  Synthetic inputs; the coefficient fields are
-16.8 MB (below the 129 MB L2), so L2 is flushed (a 256 MB write) between timed
-steps.  value = N * 100 * K / (sum of the K timed step durations).
+Default workload (--workload heat128, one bench step): the 128^3 heat problem,
+n_r = n_z = n_theta = 128, alpha = 1, dt = 1e-3, 100 BDF1 steps, T0 = 8
+Bessel x sine eigenmodes with seeded N(0,1) amplitudes, g = seeded smooth
+CCF coefficients N(0,1) * 1.25^-(i+j+|k|).  value = N * 100 * K / (sum of the
+K timed step durations).  The 16.8 MB fields sit below the 129 MB L2, so L2
+is flushed (a 256 MB write) between timed steps.
+
+Other workloads (same JSON line, for the other problem sizes of the method):
+  poisson33   -lap u = f on 33 x 33 x 32, manufactured u, values in / out
+  large512    512^3: one Poisson solve + 20 heat steps (alpha 0.1, dt 1e-4)
+  batch256    256 heat problems, n_r, n_z ~ U{32..256}, n_theta in {32,64,128},
+              alpha ~ U[0.01,1], dt 1e-3, 50 steps, T0 = 0; the plain
+              per-problem form is timed beside the batched form
+  adjoint128  128^3, alpha 0.5, dt 1e-3, 200 steps, checkpoint every 20:
+              forward run + adjoint (gradients in T0, space-time g, alpha)
 
 Legs: --impl ours (default) times the CUDA path through the C ABI; --impl
 reference times the FP64 CPU oracle on the host cores on a bounded sample of
@@ -33,7 +42,6 @@ from paper_2206_04827_gb300 import inputs  # noqa: E402
 M = N_Z = P = 128
 ALPHA, DT, NSTEPS, TOL = 1.0, 1e-3, 100, 1e-14
 SEED = 1001
-WORKLOAD = 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, 100 BDF1 steps, 8 Bessel x sine eigenmodes + smooth forcing'
 METRIC = 'FP64 unknowns*steps/s at <=1e-12 rel err'
 UNIT = 'unknowns*steps/s'
 SM_COUNT = 152
@@ -41,31 +49,29 @@ FP64_FMA_PER_CLK_PER_SM = 2      # measured: 1192 GFLOP/s at 1980 MHz on 152 SMs
 
 
 # ----------------------------------------------------------------- CPU oracle leg
+def _host_inputs_coeffs(rng):
+    """Smooth seeded coefficients used by the CPU legs (the CPU legs time
+    throughput on the 128^3 heat workload's shapes and parameters)."""
+    X0 = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
+    g = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
+    return X0, g
+
+
 def _oracle_worker(args):
     """One oracle run on a subset of slices (runs in a spawned process)."""
     os.environ.setdefault('OMP_NUM_THREADS', '1')
     sys.path.insert(0, ROOT)
     from oracle import heat as oheat
     slices, steps = args
-    rng = inputs.rng_for(SEED)
-    X0, g = _host_inputs_coeffs(rng)
+    X0, g = _host_inputs_coeffs(inputs.rng_for(SEED))
     t0 = time.perf_counter()
     out = oheat.heat_steps(X0, g, ALPHA, DT, steps, slices=slices)
-    dt = time.perf_counter() - t0
-    return dt, {s: out[s] for s in slices}
-
-
-def _host_inputs_coeffs(rng):
-    """Smooth seeded coefficients used by the CPU legs (T0 and g drawn from the
-    same generator as the GPU leg's g; the CPU legs time throughput only)."""
-    X0 = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
-    g = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
-    return X0, g
+    return time.perf_counter() - t0, {s: out[s] for s in slices}
 
 
 def run_oracle_sample(nslices=16, steps=8, procs=None):
-    """Time the oracle as it stands on `nslices` slices x `steps` steps,
-    one slice per spawned process (BLAS single-threaded in each)."""
+    """Time the oracle as it stands on `nslices` slices x `steps` steps of the
+    128^3 heat workload, one slice per spawned process (BLAS single-threaded)."""
     procs = procs or os.cpu_count() or 1
     sl = [int(s) for s in np.linspace(0, P - 1, nslices).round()]
     ctx = mp.get_context('spawn')
@@ -76,8 +82,7 @@ def run_oracle_sample(nslices=16, steps=8, procs=None):
     out = {}
     for _, d in res:
         out.update(d)
-    rate = nslices * M * N_Z * steps / wall
-    return rate, wall, min(procs, nslices), sl, out
+    return nslices * M * N_Z * steps / wall, wall, min(procs, nslices), sl, out
 
 
 # ----------------------------------------------------------------- clocks
@@ -123,28 +128,278 @@ def _local_rank():
     return int(os.environ.get('LOCAL_RANK', '0'))
 
 
-# ----------------------------------------------------------------- flop count
 def adi_flops_per_launch(plan, nsteps):
-    """Algorithmic FP64 flops of one fused launch (2 per FMA): per item and step,
-    the right side (3 + 5 FMA per element), Algorithm 1 (radial sweep 12,
-    vertical sweep 8 FMA-class ops per element and iteration; the first
-    iteration has no radial apply (-6), the last no vertical apply (-4)) and
-    the Dirichlet expansion (3 adds per element)."""
-    total = 0.0
-    h = P // 2
-    for k in range(h + 1):
-        pr = k % 2
-        J = plan.shifts(1, k, pr)[0]
-        nsl = 1 if k in (0, h) else 2
-        Mr = (M - 2 - pr + 1) // 2
-        Mf = (M - pr + 1) // 2
-        for pz in (0, 1):
-            Nz = (N_Z - 2 - pz + 1) // 2
-            Nf = (N_Z - pz + 1) // 2
-            W = nsl * Nz
-            per_step = 3 * Mf * W + 5 * Mr * W + (12 * J - 6 + 8 * J - 4) * Mr * W + 1.5 * Mf * nsl * Nf
-            total += 2.0 * per_step * nsteps
-    return total
+    """Algorithmic FP64 flops of one fused heat launch (the library's count)."""
+    return plan.flops(1, nsteps)
+
+
+# ----------------------------------------------------------------- workloads
+class Workload:
+    """units: unknowns*steps per bench step; flops: algorithmic FP64 flops of
+    the dominant kernel per bench step; launches: our kernel launches per step."""
+    name = ''
+    config = {}
+
+    def reset(self):
+        pass
+
+    def e2e_bytes(self):
+        return 0, 0
+
+
+class Heat128(Workload):
+    name = 'heat128'
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        self.torch = torch
+        self.plan = cyl.Plan(M, N_Z, P, ALPHA, DT, TOL, poisson=False, heat=True, stream=stream.cuda_stream)
+        r, z, th = self.plan.grid()
+        rng = inputs.rng_for(SEED)
+        modes = inputs.eigenmode_list(8, rng)
+        self.T0 = torch.empty(P, M, N_Z, dtype=torch.float64, device=dev)
+        self.plan.vals2coeffs(torch.as_tensor(inputs.eigenmode_values(r, z, th, modes), device=dev), self.T0)
+        self.g = torch.as_tensor(inputs.smooth_coeffs(P, M, N_Z, 1.25, rng), device=dev)
+        self.T = torch.empty_like(self.T0)
+        self.nsteps = nsteps
+        self.units = M * N_Z * P * nsteps
+        self.flops = self.plan.flops(1, nsteps)
+        self.launches = 1
+        self.kernel = 'adi_kernel'
+        self.config = {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF1 steps, '
+                                   '8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
+                       'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nsteps, 'adi_tol': TOL}
+        self.host = None
+
+    def reset(self):
+        self.T.copy_(self.T0)
+
+    def step(self):
+        self.plan.heat_step(self.T, self.g, self.nsteps)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.T0.cpu().pin_memory(), self.g.cpu().pin_memory(),
+                     t.empty(self.T0.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        T0h, gh, outh = self.host
+        self.T.copy_(T0h, non_blocking=True)
+        self.g.copy_(gh, non_blocking=True)
+        self.step()
+        outh.copy_(self.T, non_blocking=True)
+
+    def e2e_bytes(self):
+        T0h, gh, outh = self.host
+        return T0h.numel() * 8 + gh.numel() * 8, outh.numel() * 8
+
+
+class Poisson33(Workload):
+    name = 'poisson33'
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        m, n, p = 33, 33, 32
+        self.torch = torch
+        self.plan = cyl.Plan(m, n, p, adi_tol=1e-13, stream=stream.cuda_stream)
+        r, z, th = self.plan.grid()
+        self.f = torch.as_tensor(inputs.manufactured_f(r, z, th), device=dev)
+        self.u = torch.empty_like(self.f)
+        self.units = m * n * p
+        self.flops = self.plan.flops(0, 1)
+        self.launches = 7
+        self.kernel = 'adi_kernel'
+        self.config = {'workload': 'Poisson 33 x 33 x 32, manufactured u = (1-r^2)(1-z^2)exp(r cos th + z/2), '
+                                   'values in / values out, adi_tol 1e-13', 'n_r': m, 'n_z': n, 'n_theta': p}
+        self.host = None
+        self.cyl = cyl
+
+    def step(self):
+        self.plan.poisson(self.f, self.u, self.cyl.VALUES)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.f.cpu().pin_memory(), t.empty(self.f.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        fh, uh = self.host
+        self.f.copy_(fh, non_blocking=True)
+        self.step()
+        uh.copy_(self.u, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.host[0].numel() * 8, self.host[1].numel() * 8
+
+
+class Large512(Workload):
+    name = 'large512'
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        m = n = p = 512
+        self.torch, self.cyl = torch, cyl
+        self.plan = cyl.Plan(m, n, p, 0.1, 1e-4, TOL, poisson=True, heat=True, stream=stream.cuda_stream)
+        rng = inputs.rng_for(1002)
+        self.f = torch.as_tensor(inputs.smooth_coeffs(p, m, n, 1.1, rng), device=dev)
+        self.T = torch.empty_like(self.f)
+        self.hsteps = 20
+        self.units = m * n * p * (1 + self.hsteps)
+        self.flops = self.plan.flops(0, 1) + self.plan.flops(1, self.hsteps)
+        self.launches = 2
+        self.kernel = 'adi_kernel'
+        self.config = {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
+                                   'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out',
+                       'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL}
+        self.host = None
+
+    def step(self):
+        self.plan.poisson(self.f, self.T, self.cyl.COEFFS)
+        self.plan.heat_step(self.T, self.f, self.hsteps)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.f.cpu().pin_memory(), t.empty(self.f.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        fh, uh = self.host
+        self.f.copy_(fh, non_blocking=True)
+        self.step()
+        uh.copy_(self.T, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.host[0].numel() * 8, self.host[1].numel() * 8
+
+
+class Batch256(Workload):
+    name = 'batch256'
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        self.torch, self.cyl, self.stream = torch, cyl, stream
+        rng = inputs.rng_for(1003)
+        k = 256
+        self.n_r = rng.integers(32, 257, size=k)
+        self.n_z = rng.integers(32, 257, size=k)
+        self.n_t = rng.choice([32, 64, 128], size=k)
+        self.alpha = rng.uniform(0.01, 1.0, size=k)
+        self.steps = 50
+        self.bp = cyl.BatchPlan(self.n_r, self.n_z, self.n_t, self.alpha, DT, TOL, stream=stream.cuda_stream)
+        g = np.concatenate([inputs.smooth_coeffs(p, m, n, 1.25, rng).ravel() for p, m, n in self.bp.shapes])
+        self.g = torch.as_tensor(g, device=dev)
+        self.T = torch.zeros_like(self.g)
+        self.tune_ms = self.bp.autotune(self.T, self.g, 1)
+        self.units = self.bp.N * self.steps
+        self.flops = self.bp.flops(self.steps)
+        self.launches = 2
+        self.kernel = 'adi_batch_kernel'
+        thr, G, counts = self.bp.config()
+        self.config = {'workload': '256 heat problems, n_r, n_z ~ U{32..256}, n_theta ~ {32,64,128}, '
+                                   'alpha ~ U[0.01,1], dt 1e-3, 50 BDF1 steps, T0 = 0, smooth forcing (decay 1.25)',
+                       'problems': k, 'unknowns': int(self.bp.N), 'autotuned': {'threshold': thr, 'groups': G,
+                                                                             'items_per_class': list(counts)}}
+        self.host = None
+
+    def reset(self):
+        self.T.zero_()
+
+    def step(self):
+        self.bp.heat_step(self.T, self.g, self.steps)
+
+    def plain_rate(self):
+        """The plain per-problem form: one plan and one fused launch per problem."""
+        t = self.torch
+        plans, Ts, gs = [], [], []
+        for i, (p, m, n) in enumerate(self.bp.shapes):
+            plans.append(self.cyl.Plan(m, n, p, float(self.alpha[i]), DT, TOL, poisson=False, heat=True,
+                                       stream=self.stream.cuda_stream))
+            Ts.append(t.zeros(p, m, n, dtype=t.float64, device=self.g.device))
+            gs.append(self.bp.view(self.g, i))
+        for pl, T, g in zip(plans, Ts, gs):      # warm-up
+            pl.heat_step(T, g, 1)
+        t.cuda.synchronize()
+        e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+        for T in Ts:
+            T.zero_()
+        e0.record(self.stream)
+        for pl, T, g in zip(plans, Ts, gs):
+            pl.heat_step(T, g, self.steps)
+        e1.record(self.stream)
+        t.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        for pl in plans:
+            pl.close()
+        return self.units / sec
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.g.cpu().pin_memory(), t.empty(self.g.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        gh, outh = self.host
+        self.T.zero_()
+        self.g.copy_(gh, non_blocking=True)
+        self.step()
+        outh.copy_(self.T, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.host[0].numel() * 8, self.host[1].numel() * 8
+
+
+class Adjoint128(Workload):
+    name = 'adjoint128'
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        self.torch = torch
+        self.steps, self.every = 200, 20
+        self.plan = cyl.Plan(M, N_Z, P, 0.5, DT, TOL, poisson=False, heat=True, stream=stream.cuda_stream)
+        r, z, th = self.plan.grid()
+        rng = inputs.rng_for(1004)
+        self.T0 = torch.empty(P, M, N_Z, dtype=torch.float64, device=dev)
+        self.plan.vals2coeffs(torch.as_tensor(inputs.eigenmode_values(r, z, th, inputs.eigenmode_list(8, rng)),
+                                              device=dev), self.T0)
+        self.g = torch.stack([torch.as_tensor(inputs.smooth_coeffs(P, M, N_Z, 1.25, rng), device=dev)
+                              for _ in range(self.steps)])
+        self.tgt = torch.as_tensor(inputs.smooth_coeffs(P, M, N_Z, 1.25, rng), device=dev)
+        w = torch.full((P, 1, 1), 2.0, dtype=torch.float64, device=dev)
+        w[0] = w[P - 1] = 1.0
+        self.w = w
+        self.T = torch.empty_like(self.T0)
+        self.dT0 = torch.empty_like(self.T0)
+        self.dg = torch.empty_like(self.g)
+        self.dal = torch.zeros(1, dtype=torch.float64, device=dev)
+        nb = self.plan.adjoint_workspace_bytes(self.steps, self.every, True)
+        self.ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device=dev)
+        Nn = M * N_Z * P
+        self.units = Nn * self.steps
+        # forward + checkpoint pass + recompute pass (heat kernel) and the transposed pass
+        self.flops = 3 * self.plan.flops(1, self.steps) + self.plan.flops(1, self.steps, transposed=True)
+        self.launches = 1 + 1 + 2 * (self.steps // self.every) + 1
+        self.kernel = 'adi_kernel + adi_adjoint_kernel'
+        self.config = {'workload': 'adjoint 128^3, alpha 0.5, dt 1e-3, 200 BDF1 steps, checkpoint every 20: '
+                                   'forward run + gradients of |T_N - T_target|^2 in T0, space-time g and alpha',
+                       'n_r': M, 'n_z': N_Z, 'n_theta': P, 'units': 'unknowns x 200 steps per gradient evaluation'}
+        self.host = None
+
+    def step(self):
+        N = M * N_Z * P
+        self.T.copy_(self.T0)
+        self.plan.heat_step(self.T, self.g, self.steps, g_step_stride=N)
+        lam = 2.0 * self.w * (self.T - self.tgt)
+        self.plan.heat_adjoint(self.T0, self.g, self.steps, lam, self.dT0, self.dg, self.dal, g_step_stride=N,
+                               ckpt_every=self.every, workspace=self.ws)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.T0.cpu().pin_memory(), t.empty(self.T0.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        T0h, outh = self.host
+        self.T0.copy_(T0h, non_blocking=True)
+        self.step()
+        outh.copy_(self.dT0, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.host[0].numel() * 8, self.host[1].numel() * 8
+
+
+WORKLOADS = {'heat128': Heat128, 'poisson33': Poisson33, 'large512': Large512, 'batch256': Batch256,
+             'adjoint128': Adjoint128}
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -160,41 +415,26 @@ def run_ours(args):
 
     # CPU baseline and accuracy sample first (spawned pool before heavy GPU use)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == 'heat128':
         rate, wall, cores, sl, oracle_out = run_oracle_sample(args.cpu_slices, args.cpu_steps)
         cpu = dict(value=rate, wall=wall, cores=cores, slices=sl, out=oracle_out)
 
     from paper_2206_04827_gb300 import cyl
     stream = torch.cuda.current_stream(dev)
-    plan = cyl.Plan(M, N_Z, P, ALPHA, DT, TOL, poisson=False, heat=True, stream=stream.cuda_stream)
-    r, z, th = plan.grid()
-    rng = inputs.rng_for(SEED)
-    modes = inputs.eigenmode_list(8, rng)
-    g_host = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
-    T0 = torch.empty(P, M, N_Z, dtype=torch.float64, device=dev)
-    plan.vals2coeffs(torch.as_tensor(inputs.eigenmode_values(r, z, th, modes), device=dev), T0)
-    g = torch.as_tensor(g_host, device=dev)
-    T = torch.empty_like(T0)
+    wl = WORKLOADS[args.workload](cyl, torch, dev, stream, args.nsteps)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    Nunk = M * N_Z * P
-
-    nst = args.nsteps
-
-    def one_step():
-        plan.heat_step(T, g, nst)
 
     for _ in range(args.warmup):
-        T.copy_(T0)
-        one_step()
+        wl.reset()
+        wl.step()
     torch.cuda.synchronize()
 
-    # accuracy: the same run compared with the oracle on the sampled slices
+    # accuracy: the 128^3 heat run compared with the oracle on the sampled slices
     acc = None
     if cpu is not None:
-        rng2 = inputs.rng_for(SEED)
-        X0c, gc = _host_inputs_coeffs(rng2)
+        X0c, gc = _host_inputs_coeffs(inputs.rng_for(SEED))
         Tc = torch.as_tensor(X0c, device=dev)
-        plan.heat_step(Tc, torch.as_tensor(gc, device=dev), args.cpu_steps)
+        wl.plan.heat_step(Tc, torch.as_tensor(gc, device=dev), args.cpu_steps)
         Tc = Tc.cpu().numpy()
         ref = np.stack([cpu['out'][s] for s in cpu['slices']])
         got = np.stack([Tc[s] for s in cpu['slices']])
@@ -209,12 +449,12 @@ def run_ours(args):
     evs = []
     wall0 = time.perf_counter()
     for _ in range(args.steps):
-        T.copy_(T0)
+        wl.reset()
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one_step()
+        wl.step()
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
@@ -222,62 +462,59 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    durs = [a.elapsed_time(b) * 1e-3 for a, b in evs]
-    t_sum = sum(durs)
+    t_sum = sum(a.elapsed_time(b) * 1e-3 for a, b in evs)
     t_max = torch.tensor([t_sum], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     t_sum = float(t_max.item())
 
     # end to end through the C ABI with pinned host buffers
-    T0_h = T0.cpu().pin_memory()
-    g_h = g.cpu().pin_memory()
-    out_h = torch.empty_like(T0_h).pin_memory()
+    wl.e2e_setup()
     e2e = []
-    for it in range(args.steps + 1):
+    for it in range(max(2, min(args.steps, 3)) + 1):
+        wl.reset()
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        T.copy_(T0_h, non_blocking=True)
-        g.copy_(g_h, non_blocking=True)
-        one_step()
-        out_h.copy_(T, non_blocking=True)
+        wl.e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
         if it > 0:
             e2e.append(e0.elapsed_time(e1) * 1e-3)
-    e2e_t = sum(e2e)
+    h2d, d2h = wl.e2e_bytes()
 
-    flops = adi_flops_per_launch(plan, nst)
     peak_mhz = clocks['sm_max_mhz'] or 2070.0
     peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * peak_mhz * 1e6
-    achieved = flops / (t_sum / args.steps)
+    achieved = wl.flops / (t_sum / args.steps)
     line = {
-        'metric': METRIC, 'value': world * Nunk * nst * args.steps / t_sum, 'unit': UNIT,
+        'metric': METRIC, 'value': world * wl.units * args.steps / t_sum, 'unit': UNIT,
         'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
         'ms_per_step': 1e3 * t_sum / args.steps, 'higher_is_better': True, 'scaling': 'weak',
         'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': WORKLOAD, 'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nst,
-                   'adi_tol': TOL, 'l2': 'flushed between timed steps (256 MB write)',
-                   'parallelism': 'replicas' if world > 1 else 'single'},
+        'config': dict(wl.config, l2='flushed between timed steps (256 MB write)',
+                       parallelism='replicas' if world > 1 else 'single'),
         'roofline': {'bound': 'alu', 'achieved': achieved / 1e12, 'peak': peak / 1e12, 'unit': 'TFLOP/s',
                      'frac': achieved / peak, 'traffic': None,
                      'peak_basis': '152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (of derived)',
-                     'kernel': 'adi_kernel'},
-        'e2e': {'value': world * Nunk * nst * len(e2e) / e2e_t, 'unit': UNIT,
-                'h2d_bytes_per_step': int(T0_h.numel() * 8 + g_h.numel() * 8),
-                'd2h_bytes_per_step': int(out_h.numel() * 8)},
-        'gpu_launches': args.steps,
+                     'kernel': wl.kernel},
+        'e2e': {'value': world * wl.units * len(e2e) / sum(e2e), 'unit': UNIT,
+                'h2d_bytes_per_step': int(h2d), 'd2h_bytes_per_step': int(d2h)},
+        'gpu_launches': wl.launches * args.steps,
         'clocks': {k: clocks[k] for k in ('sm_mhz', 'sm_max_mhz', 'reasons')},
         'wall_s': wall,
     }
     if cpu is not None:
         line['cpu_baseline'] = {'value': cpu['value'], 'unit': UNIT, 'cores': cpu['cores'], 'kind': 'oracle',
-                                'sample': '%d of %d theta-slices x %d BDF1 steps of the 128^3 problem '
+                                'sample': '%d of %d theta-slices x %d BDF1 steps of the 128^3 heat problem '
                                           '(QZ Bartels-Stewart per slice, one process per slice)'
                                           % (len(cpu['slices']), P, args.cpu_steps)}
         line['max_rel_err_vs_oracle'] = acc
+    if isinstance(wl, Batch256):
+        plain = wl.plain_rate()
+        line['plain_per_problem_value'] = world * plain
+        line['batched_over_plain'] = line['value'] / (world * plain)
+        line['autotune_ms'] = wl.tune_ms
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -290,19 +527,19 @@ def run_reference(args):
         return
     for _ in range(args.warmup):
         run_oracle_sample(args.cpu_slices, 1)
-    rates, walls = [], []
+    walls, cores = [], 1
     for _ in range(args.steps):
-        rate, wall, cores, sl, _ = run_oracle_sample(args.cpu_slices, args.cpu_steps)
-        rates.append(rate)
+        _, wall, cores, _, _ = run_oracle_sample(args.cpu_slices, args.cpu_steps)
         walls.append(wall)
-    value = len(rates) * args.cpu_slices * M * N_Z * args.cpu_steps / sum(walls)
-    sample = '%d of %d theta-slices x %d BDF1 steps of the 128^3 problem per bench step' % (
+    value = len(walls) * args.cpu_slices * M * N_Z * args.cpu_steps / sum(walls)
+    sample = '%d of %d theta-slices x %d BDF1 steps of the 128^3 heat problem per bench step' % (
         args.cpu_slices, P, args.cpu_steps)
     print(json.dumps({
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': 0, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': 1e3 * sum(walls) / len(walls), 'higher_is_better': True,
         'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': WORKLOAD, 'n_r': M, 'n_z': N_Z, 'n_theta': P},
+        'config': {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, BDF1, smooth forcing',
+                   'n_r': M, 'n_z': N_Z, 'n_theta': P},
         'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle', 'sample': sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }), flush=True)
@@ -314,11 +551,12 @@ def main():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--workload', default='heat128', choices=sorted(WORKLOADS))
     ap.add_argument('--cpu-slices', type=int, default=16)
     ap.add_argument('--cpu-steps', type=int, default=10)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--nsteps', type=int, default=NSTEPS,
-                    help='BDF1 steps per bench step (100 = the workload; fewer only for profiling)')
+                    help='BDF1 steps per bench step of heat128 (100 = the workload; fewer only for profiling)')
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -284,6 +284,14 @@ cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int pari
  * Any pointer may be NULL. */
 cyl_status cyl_grid(cyl_plan_t plan, double *r, double *z, double *theta);
 
+/* Algorithmic FP64 flops of nsteps steps of the fused ADI kernel (which: 0
+ * Poisson, 1 heat; transposed: 0 forward, 1 adjoint), counting 2 per fused
+ * multiply-add: the right side (3 + 5 per element), Algorithm 1 (radial
+ * sweep 12 and vertical sweep 8 per element and iteration, minus the radial
+ * apply of the first and the vertical apply of the last iteration) and the
+ * Dirichlet expansion.  Host only; valid for batch plans (which = 1). */
+cyl_status cyl_plan_flops(cyl_plan_t plan, int which, int nsteps, int transposed, double *flops);
+
 /* Complete elliptic integral K as a function of the complementary modulus
  * k' (so that k = sqrt(1 - k'^2) never loses precision), and the Jacobi
  * function dn(u | k) with the same argument convention (DLMF 19.8, 22.20). */

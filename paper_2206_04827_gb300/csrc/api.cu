@@ -526,6 +526,28 @@ cyl_status cyl_sync(cyl_plan_t P) {
   return CYL_OK;
 }
 
+cyl_status cyl_plan_flops(cyl_plan_t P, int which, int nsteps, int transposed, double *flops) {
+  if (!P || !flops || which < 0 || which > 1 || nsteps < 0) return CYL_EINVAL;
+  const std::vector<Item> &items = P->is_batch ? P->bitems : P->hp.kind[which].items;
+  if (P->is_batch && which != 1) return CYL_ESTATE;
+  double f = 0.0;
+  for (const Item &it : items) {
+    const double W = (double)it.nsl * it.Nz, M = it.M;
+    double per_step;
+    if (!transposed) {
+      per_step = 3.0 * it.Mfull * W + 5.0 * M * W + (12.0 * it.J - 6.0 + 8.0 * it.J - 4.0) * M * W +
+                 1.5 * it.Mfull * it.nsl * it.Nzfull;
+    } else {
+      const double Wf = (double)it.nsl * it.Nzfull;
+      per_step = 1.5 * M * W + (12.0 * it.J - 6.0 + 8.0 * it.J - 4.0) * M * W + 3.0 * M * Wf +
+                 5.0 * it.Mfull * Wf;
+    }
+    f += 2.0 * per_step * nsteps;   // 2 flops per fused multiply-add
+  }
+  *flops = f;
+  return CYL_OK;
+}
+
 cyl_status cyl_grid(cyl_plan_t P, double *r, double *z, double *theta) {
   if (!P) return CYL_EINVAL;
   if (P->is_batch) return CYL_ESTATE;

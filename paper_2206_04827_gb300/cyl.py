@@ -46,6 +46,7 @@ _sig = {
     'cyl_plan_operator': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), _c_double_p]),
     'cyl_grid': (ctypes.c_int, [_vp, _c_double_p, _c_double_p, _c_double_p]),
+    'cyl_plan_flops': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_double_p]),
     'cyl_plan_batch': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
@@ -188,6 +189,10 @@ class Plan:
         _check(_lib.cyl_grid(self._h, r, z, t), 'cyl_grid')
         return np.array(r), np.array(z), np.array(t)
 
+    def flops(self, which, nsteps, transposed=False):
+        """Algorithmic FP64 flops of nsteps steps (see include/cyl.h: cyl_plan_flops)."""
+        return plan_flops(self._h, which, nsteps, transposed)
+
     def shifts(self, which, k, parity):
         """(J, (a, b, c, d), p_shifts, q_shifts) of one wavenumber (host tables)."""
         J = ctypes.c_int()
@@ -261,10 +266,20 @@ class BatchPlan:
     def sync(self):
         _check(_lib.cyl_sync(self._h), 'cyl_sync')
 
+    def flops(self, nsteps):
+        return plan_flops(self._h, 1, nsteps, False)
+
     def view(self, T, i):
         """Problem i's [p][m][n] view of a batch array."""
         p, m, n = self.shapes[i]
         return T[self.offsets[i]:self.offsets[i + 1]].view(p, m, n)
+
+
+def plan_flops(handle, which, nsteps, transposed):
+    f = ctypes.c_double()
+    _check(_lib.cyl_plan_flops(handle, int(which), int(nsteps), int(bool(transposed)), ctypes.byref(f)),
+           'cyl_plan_flops')
+    return f.value
 
 
 def exported_symbols():
