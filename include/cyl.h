@@ -61,6 +61,10 @@ typedef enum {
 #define CYL_BOTH_PARITIES  4u  /* solve both radial parity blocks                */
 #define CYL_HOST_ONLY      8u  /* host tables only: no device memory, no kernels */
 #define CYL_FORCE_GLOBAL  16u  /* keep ADI work arrays in global memory          */
+/* Failure-detection test only: the ADI kernels never start their factor-table
+ * copies, so every bounded device wait runs out (after about 1 ms) and
+ * cyl_sync reports CYL_ETIMEOUT; the results of such a plan are garbage. */
+#define CYL_TEST_NO_TMA   32u
 
 /* space selector of cyl_poisson */
 #define CYL_VALUES 0

@@ -56,6 +56,8 @@ struct cyl_plan_s {
 namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024 - 1024;   // opt-in limit minus static shared memory
+constexpr long long kWaitCycles = 2000000000LL;     // bounded device waits: about 1 s at 2 GHz
+constexpr long long kTestWaitCycles = 2000000LL;    // about 1 ms under CYL_TEST_NO_TMA
 
 template <class T>
 cudaError_t upload(T **dst, const T *src, size_t count) {
@@ -135,6 +137,8 @@ cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
   a.maxNz = P->maxNz;
   a.err = P->d_err;
   a.ckpt_every = 1;
+  a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
+  a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
   return a;
 }
 
@@ -165,6 +169,8 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   a.maxM = P->maxM;
   a.maxNz = P->maxNz;
   a.err = P->d_err;
+  a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
+  a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
@@ -272,6 +278,7 @@ cyl_status run_batch(cyl_plan_s *P, double *T, const double *g, int nsteps) {
     a.maxM = C.maxM;
     a.maxNz = C.maxNz;
     a.err = P->d_err;
+    a.wait_limit = kWaitCycles;
     a.group_doubles = (long long)cyl::batch_group_doubles(C.ld, C.smem_rows, C.maxM, C.maxNz);
     if (a.group_doubles % 32 != 0 || (size_t)a.group_doubles * C.G * sizeof(double) > C.smem) return CYL_EINVAL;
     cudaStream_t st = (two && cls == 1) ? P->aux : P->st;
@@ -311,7 +318,8 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   if (n_r < 4 || n_z < 4 || n_theta < 2 || (n_theta & 1)) return CYL_EINVAL;
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
   if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT))) return CYL_EINVAL;
-  if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL))
+  if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL |
+                          CYL_TEST_NO_TMA))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if ((long long)n_r * n_z * n_theta > (1LL << 40)) return CYL_EINVAL;

@@ -51,9 +51,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                : "memory");
 }
 
-// Bounded wait on an mbarrier phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 24); ++it) {
+// Bounded wait on an mbarrier phase: false once `limit` SM clock cycles have
+// passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  for (;;) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -61,8 +63,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (clock64() - t0 > limit) return false;
   }
-  return false;
 }
 
 // One ADI iteration of Algorithm 1 in the form
@@ -292,11 +294,11 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, ld = a.ld, J = it.J;
   for (int jt = 0; jt < J; ++jt, ++c) {
     const int buf = (int)(c & 1);
-    if (gp.tid == 0 && c + 1 < c_end) {
+    if (gp.tid == 0 && c + 1 < c_end && !a.test_no_tma) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_tables<TRANS>(sh, a, it, c + 1, c0);
     }
-    if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1))) timed_out = true;
+    if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1), a.wait_limit)) timed_out = true;
     const double *RB = sh.RB0 + buf * sh.rlen;
     const double *ZB = sh.ZB0 + buf * sh.zlen;
     for (int col = gp.tid; col < W; col += gp.nth) {
@@ -335,7 +337,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
   const double *r2 = a.fac + it.r2off;
   const double *c02 = a.fac + it.c02off;
   const long long c0 = c, c_end = c0 + (long long)a.nsteps * it.J;
-  if (tid == 0) issue_tables<false>(sh, a, it, c0, c0);
+  if (tid == 0 && !a.test_no_tma) issue_tables<false>(sh, a, it, c0, c0);
   const double *Xsrc = a.Xin + it.xoff;
   double *Xout = a.Xout + it.xoff;
   const double *Gbase = a.G ? a.G + it.xoff : nullptr;
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
   const double *c02 = a.fac + it.c02off;
   const int nst = g.n_hi - g.n_lo;
   const long long total_it = (long long)nst * it.J;
-  if (tid == 0) issue_tables<true>(sh, a, it, 0, 0);
+  if (tid == 0 && !a.test_no_tma) issue_tables<true>(sh, a, it, 0, 0);
   bool timed_out = false;
   double apart = 0.0;
   double *lam = g.lam;

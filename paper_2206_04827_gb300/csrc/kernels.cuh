@@ -31,6 +31,8 @@ struct AdiArgs {
   int maxM, maxNz;         // band table sizes in shared memory
   int *err;                // device status word (CYL_ERR_TIMEOUT on a bounded-wait timeout)
   long long group_doubles; // batch kernel: shared-memory slice per thread group (multiple of 32)
+  long long wait_limit;    // SM clock cycles a bounded wait may spin (about 1 s normally)
+  int test_no_tma;         // failure-detection test: never start table copies, so waits run out
 };
 
 constexpr int CYL_ERR_TIMEOUT = 4;

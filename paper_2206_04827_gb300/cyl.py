@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # status codes and flags (include/cyl.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
-WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL = 1, 2, 4, 8, 16
+WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA = 1, 2, 4, 8, 16, 32
 VALUES, COEFFS = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -104,10 +104,10 @@ class Plan:
     """Owner of one ``cyl_plan_t`` (see include/cyl.h: cyl_plan)."""
 
     def __init__(self, n_r, n_z, n_theta, alpha=0.0, dt=0.0, adi_tol=1e-14, poisson=True, heat=False,
-                 both_parities=False, host_only=False, force_global=False, stream=None):
+                 both_parities=False, host_only=False, force_global=False, stream=None, extra_flags=0):
         flags = (WITH_POISSON if poisson else 0) | (WITH_HEAT if heat else 0) \
             | (BOTH_PARITIES if both_parities else 0) | (HOST_ONLY if host_only else 0) \
-            | (FORCE_GLOBAL if force_global else 0)
+            | (FORCE_GLOBAL if force_global else 0) | int(extra_flags)
         if stream is None and not host_only:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

@@ -163,3 +163,23 @@ def test_heat_128_sampled_slices_match_oracle(cyl):
     scale = np.abs(want[sl]).max()
     for s in sl:
         assert np.abs(got[s] - want[s]).max() / scale <= TOL_SOLVE, s
+
+
+def test_bounded_wait_timeout_is_reported(cyl):
+    """Failure detection without a GPU fault: under CYL_TEST_NO_TMA no table
+    copy is ever started, every bounded wait runs out, cyl_sync reports
+    CYL_ETIMEOUT, and the context stays usable afterwards."""
+    p, m, n = 4, 9, 8
+    X0 = inputs.smooth_coeffs(p, m, n, 1.3, np.random.default_rng(1))
+    bad = cyl.Plan(m, n, p, 0.5, 1e-2, 1e-12, poisson=False, heat=True, extra_flags=cyl.TEST_NO_TMA)
+    T = dev(X0)
+    bad.heat_step(T, None, 1)
+    with pytest.raises(cyl.CylError) as ei:
+        bad.sync()
+    assert ei.value.status == cyl.ETIMEOUT
+    bad.sync()                                        # the flag was cleared
+    good = cyl.Plan(m, n, p, 0.5, 1e-2, 1e-14, poisson=False, heat=True)
+    T = dev(X0)
+    good.heat_step(T, None, 2)
+    good.sync()
+    assert relerr(host(T), oheat.heat_steps(X0, np.zeros_like(X0), 0.5, 1e-2, 2)) <= TOL_SOLVE
