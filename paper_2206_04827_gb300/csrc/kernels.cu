@@ -83,7 +83,7 @@ __device__ __forceinline__ double comp(const double2 *a) {
   return (K & 1) ? a[K >> 1].y : a[K >> 1].x;
 }
 
-template <bool FIRST, bool TRANS>
+template <bool FIRST, bool TRANS, int UNR>
 __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const double *__restrict__ Fc, int ld,
                                              const double *__restrict__ RB, int M) {
   constexpr int LO = TRANS ? 3 : 2, HI = TRANS ? 2 : 3;     // apply band offsets [-LO, HI]
@@ -107,6 +107,7 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
   double y[LBW];
 #pragma unroll
   for (int k = 0; k < LBW; ++k) y[k] = 0.0;
+#pragma unroll UNR
   for (int i = 0; i < M; ++i) {
     const double f = fn;
     double2 rec[NF];
@@ -132,9 +133,10 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
 #pragma unroll
       for (int k = 0; k < LO + HI; ++k) w[k] = w[k + 1];
     }
-    acc = fma(comp<6>(rec), y[0], acc);
-    acc = fma(comp<7>(rec), y[1], acc);
+    // L terms, oldest first: only the last one waits for the previous row
     if (LBW == 3) acc = fma(comp<(LBW == 3 ? 8 : 7)>(rec), y[LBW - 1], acc);
+    acc = fma(comp<7>(rec), y[1], acc);
+    acc = fma(comp<6>(rec), y[0], acc);
     col[i * ld] = acc;
 #pragma unroll
     for (int l = LBW - 1; l > 0; --l) y[l] = y[l - 1];
@@ -147,6 +149,7 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
   double2 nb[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k) nb[k] = rb2[(M - 1) * (RSTRIDE / 2) + B0 + k];
+#pragma unroll UNR
   for (int i = M - 1; i >= 0; --i) {
     const double yv = yn;
     double2 cb[NB];
@@ -157,10 +160,11 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
 #pragma unroll
       for (int k = 0; k < NB; ++k) nb[k] = rb2[(i - 1) * (RSTRIDE / 2) + B0 + k];
     }
-    double acc = fma(comp<6 + LBW - 2 * B0>(cb), z[0], yv);
-    acc = fma(comp<7 + LBW - 2 * B0>(cb), z[1], acc);
+    // U terms carry the pivot; the newest value z_{i+1} enters last
+    double acc = comp<11 - 2 * B0>(cb) * yv;
     if (UBW == 3) acc = fma(comp<(UBW == 3 ? 8 + LBW - 2 * B0 : 7 + LBW - 2 * B0)>(cb), z[UBW - 1], acc);
-    const double zi = acc * comp<11 - 2 * B0>(cb);
+    acc = fma(comp<7 + LBW - 2 * B0>(cb), z[1], acc);
+    const double zi = fma(comp<6 + LBW - 2 * B0>(cb), z[0], acc);
     col[i * ld] = zi;
 #pragma unroll
     for (int u = UBW - 1; u > 0; --u) z[u] = z[u - 1];
@@ -168,7 +172,7 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
   }
 }
 
-template <bool LAST, bool TRANS>
+template <bool LAST, bool TRANS, int UNR>
 __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz) {
   constexpr int LB = TRANS ? 2 : 1;                         // L bandwidth (U: 3 - LB)
   constexpr int ALO = TRANS ? 2 : 1;                        // apply offsets [-ALO, 3 - ALO]
@@ -178,6 +182,7 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
   for (int l = 0; l < LB; ++l) wq[l] = 0.0;
   double rn = row[0];
   double2 cn = z2p[0];
+#pragma unroll UNR
   for (int b = 0; b < Nz; ++b) {
     const double r = rn;
     const double2 c = cn;
@@ -185,8 +190,9 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
       rn = row[b + 1];
       cn = z2p[(b + 1) * 4];
     }
-    double w = fma(c.x, wq[0], r);
+    double w = r;
     if (LB == 2) w = fma(c.y, wq[LB - 1], w);
+    w = fma(c.x, wq[0], w);
     row[b] = w;
 #pragma unroll
     for (int l = LB - 1; l > 0; --l) wq[l] = wq[l - 1];
@@ -199,6 +205,7 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
   double2 q45[ALO], q67[ALO];                               // apply records of columns b+1 .. b+ALO
 #pragma unroll
   for (int t = 0; t < ALO; ++t) { q45[t] = make_double2(0.0, 0.0); q67[t] = make_double2(0.0, 0.0); }
+#pragma unroll UNR
   for (int b = Nz - 1; b >= 0; --b) {
     const double wb = wn;
     const double2 c01 = p01, c23 = p23;
@@ -210,24 +217,23 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
       p23 = z2p[(b - 1) * 4 + 1];
       if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
     }
-    double v, xb;
-    if (TRANS) {            // [0..1] -L, [2] -U, [3] 1/U_cc
-      v = fma(c23.x, x1, wb);
-      xb = v * c23.y;
-    } else {                // [0] -L, [1..2] -U, [3] 1/U_cc
-      v = fma(c01.y, x1, wb);
-      v = fma(c23.x, x2, v);
-      xb = v * c23.y;
+    // U terms carry the pivot; the newest value x_{b+1} enters last
+    double xb;
+    if (TRANS) {            // [0..1] -L, [2] -U/U_cc, [3] 1/U_cc
+      xb = fma(c23.x, x1, c23.y * wb);
+    } else {                // [0] -L, [1..2] -U/U_cc, [3] 1/U_cc
+      double v = fma(c23.x, x2, c23.y * wb);
+      xb = fma(c01.y, x1, v);
     }
     if (LAST) {
       row[b] = xb;
     } else {
       if (b + ALO < Nz) {
         const double2 a45 = q45[ALO - 1], a67 = q67[ALO - 1];
-        double u = a45.x * xb;
-        u = fma(a45.y, x1, u);
+        double u = a67.y * x3;
         u = fma(a67.x, x2, u);
-        u = fma(a67.y, x3, u);
+        u = fma(a45.y, x1, u);
+        u = fma(a45.x, xb, u);
         row[b + ALO] = u;
       }
 #pragma unroll
@@ -287,7 +293,10 @@ __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs 
   bulk_g2s(sh.ZB0 + buf * sh.zlen, a.fac + zoff + (size_t)jt * it.Nz * ZSTRIDE, zbytes, &sh.bar[buf]);
 }
 
-template <bool TRANS>
+// UNR: unroll factor of the sweeps.  Measured on GB300: 2 with the work
+// arrays in shared memory; 8 with them in global memory, where more rows in
+// flight hide the load latency (1 is 6x slower there, 8 beats 4 by 15 %).
+template <bool TRANS, int UNR>
 __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &sh, const AdiArgs &a, const Item &it,
                                                double *S, const double *Fa, int ldF, long long &c, long long c0,
                                                long long c_end, bool &timed_out) {
@@ -302,14 +311,14 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const double *RB = sh.RB0 + buf * sh.rlen;
     const double *ZB = sh.ZB0 + buf * sh.zlen;
     for (int col = gp.tid; col < W; col += gp.nth) {
-      if (jt == 0) radial_sweep<true, TRANS>(S + col, Fa + col, ld, RB, M);
-      else radial_sweep<false, TRANS>(S + col, Fa + col, ld, RB, M);
+      if (jt == 0) radial_sweep<true, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
+      else radial_sweep<false, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
     }
     gp.sync();
     for (int r = gp.tid; r < nsl * M; r += gp.nth) {
       const int sl = r / M, aa = r - sl * M;
-      if (jt + 1 == J) vertical_sweep<true, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
-      else vertical_sweep<false, TRANS>(S + aa * ld + sl * Nz, ZB, Nz);
+      if (jt + 1 == J) vertical_sweep<true, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+      else vertical_sweep<false, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
     }
     gp.sync();
   }
@@ -326,6 +335,7 @@ __device__ __forceinline__ void init_bars(const Grp &gp, unsigned long long *bar
 }
 
 // Every BDF1 step of one item (see adi_kernel): right side, ADI, expansion.
+template <int UNR>
 __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArgs &a, const Item &it,
                                                      const AdiShared &sh, double *S, double *Fa, long long &c,
                                                      bool &timed_out) {
@@ -375,7 +385,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     gp.sync();
 
-    adi_iterations<false>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
+    adi_iterations<false, UNR>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
     const int Wf = nsl * it.Nzfull;
@@ -412,8 +422,8 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
 
 // One CTA per item.  S_SMEM / F_SMEM place the item's iterate (S) and right
 // side (Fa) in shared memory, else in the per-item global work area.
-template <bool S_SMEM, bool F_SMEM>
-__global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
+template <bool S_SMEM, bool F_SMEM, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
   const Item it = a.items[blockIdx.x];
@@ -432,7 +442,7 @@ __global__ void __launch_bounds__(512, 1) adi_kernel(const AdiArgs a) {
   init_bars(gp, bar);
   bool timed_out = false;
   long long c = 0;
-  process_item_forward(gp, a, it, sh, S, Fa, c, timed_out);
+  process_item_forward<S_SMEM ? 2 : 8>(gp, a, it, sh, S, Fa, c, timed_out);
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
 
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int 
     gp.sync();
     if (idx >= a.nitems) break;
     const Item it = a.items[idx];
-    process_item_forward(gp, a, it, sh, S, Fa, c, timed_out);
+    process_item_forward<2>(gp, a, it, sh, S, Fa, c, timed_out);
   }
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
       Fa[aa * ld + cc] = lam[o] - lam[o + 2] - lam[o + 2 * n] + lam[o + 2 * n + 2];
     }
     __syncthreads();
-    adi_iterations<true>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
+    adi_iterations<true, SMEM ? 2 : 8>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
     // T1 = Lambda C02 on nsl * Nzfull columns: T1[a][b'] = sum_t Lambda[a][b' - t] C02[b' - t][t]
     for (int e = tid; e < M * Wf; e += nth) {
       const int aa = e / Wf, cc = e - aa * Wf;
@@ -645,23 +655,28 @@ cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, 
   return cudaGetLastError();
 }
 
+template <bool S_SMEM, bool F_SMEM, int MAXT>
+static cudaError_t launch_adi_t(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(adi_kernel<S_SMEM, F_SMEM, MAXT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  adi_kernel<S_SMEM, F_SMEM, MAXT><<<a.nitems, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Blocks of at most 128 threads get an instantiation with a larger register
+// budget (up to 255 per thread).
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (a.use_smem == 2) {
-    e = cudaFuncSetAttribute(adi_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    adi_kernel<true, true><<<a.nitems, threads, smem, st>>>(a);
-  } else if (a.use_smem == 1) {
-    e = cudaFuncSetAttribute(adi_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    adi_kernel<true, false><<<a.nitems, threads, smem, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(adi_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    adi_kernel<false, false><<<a.nitems, threads, smem, st>>>(a);
-  }
-  return cudaGetLastError();
+  const bool small = threads <= 128;
+  if (a.use_smem == 2)
+    return small ? launch_adi_t<true, true, 128>(a, threads, smem, st)
+                 : launch_adi_t<true, true, 512>(a, threads, smem, st);
+  if (a.use_smem == 1)
+    return small ? launch_adi_t<true, false, 128>(a, threads, smem, st)
+                 : launch_adi_t<true, false, 512>(a, threads, smem, st);
+  return small ? launch_adi_t<false, false, 128>(a, threads, smem, st)
+               : launch_adi_t<false, false, 512>(a, threads, smem, st);
 }
 
 __global__ void axis_matvec_kernel(const double *__restrict__ in, double *__restrict__ out,

@@ -460,8 +460,9 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
               F.push_back((i + o >= 0 && i + o < M) ? (A.get(i, i + o) - qj * Cb[pr].get(i, i + o)) / s : 0.0);
             F.push_back(i >= 1 ? -LU.get(i, i - 1) : 0.0);
             F.push_back(i >= 2 ? -LU.get(i, i - 2) : 0.0);
-            for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s : 0.0);
-            F.push_back(s / LU.get(i, i));
+            const double dpiv = s / LU.get(i, i);
+            for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
+            F.push_back(dpiv);
           }
         }
         // transposed radial factors (adjoint of the heat step)
@@ -477,8 +478,9 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
                 F.push_back((i + o >= 0 && i + o < M)
                                 ? (A.get(i + o, i) - qj * Cb[pr].get(i + o, i)) / s : 0.0);
               for (int o = 1; o <= 3; ++o) F.push_back(i >= o ? -LU.get(i, i - o) : 0.0);
-              for (int o = 1; o <= 2; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s : 0.0);
-              F.push_back(s / LU.get(i, i));
+              const double dpiv = s / LU.get(i, i);
+              for (int o = 1; o <= 2; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
+              F.push_back(dpiv);
             }
           }
         }
@@ -494,10 +496,11 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             const bool last = (j + 1 == S.J);
             const double pn = last ? 0.0 : S.p[j + 1];
             for (int cc = 0; cc < Nz; ++cc) {
+              const double dz = 1.0 / LU.get(cc, cc);
               F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
-              F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) : 0.0);
-              F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) : 0.0);
-              F.push_back(1.0 / LU.get(cc, cc));
+              F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
+              F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) * dz : 0.0);
+              F.push_back(dz);
               for (int o = -1; o <= 2; ++o) {
                 const int l = cc + o;
                 F.push_back((!last && l >= 0 && l < Nz) ? D.get(cc, l) + pn * Bb[pz].get(cc, l) : 0.0);
@@ -513,10 +516,11 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
               const bool last = (j + 1 == S.J);
               const double pn = last ? 0.0 : S.p[j + 1];
               for (int cc = 0; cc < Nz; ++cc) {
+                const double dz = 1.0 / LU.get(cc, cc);
                 F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
                 F.push_back(cc >= 2 ? -LU.get(cc, cc - 2) : 0.0);
-                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) : 0.0);
-                F.push_back(1.0 / LU.get(cc, cc));
+                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
+                F.push_back(dz);
                 for (int o = -2; o <= 1; ++o) {
                   const int l = cc + o;
                   F.push_back((!last && l >= 0 && l < Nz) ? D.get(l, cc) + pn * Bb[pz].get(l, cc) : 0.0);

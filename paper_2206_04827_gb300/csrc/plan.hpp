@@ -30,17 +30,19 @@ struct Band {
 // pre-scaled so that one sweep computes Z = (A - pC)^-1 [(q-p) E + (A - qC) U]:
 //   [0..5]  (A - qC)[i][i+o] / (q-p),  o = -2 .. 3
 //   [6..7]  -L[i][i-1], -L[i][i-2]               (unit lower factor)
-//   [8..10] -U[i][i+o] / (q-p),  o = 1 .. 3       (upper factor)
+//   [8..10] -U[i][i+o] / U[i][i],  o = 1 .. 3     (upper factor, pivot folded in)
 //   [11]    (q-p) / U[i][i]
+// so that Z_i = [11] * y_i + [10] Z_{i+3} + [9] Z_{i+2} + [8] Z_{i+1}: the loop-carried
+// recurrence is a single fused multiply-add per row.
 constexpr int RSTRIDE = 12;
 // The transposed system (adjoint) uses the same record sizes with the band
 // orientations swapped: radial [0..5] (A - qC)^T[i][i+o]/(q-p), o = -3 .. 2;
-// [6..8] -L[i][i-1..i-3]; [9..10] -U[i][i+1..i+2]/(q-p); [11] (q-p)/U[i][i],
+// [6..8] -L[i][i-1..i-3]; [9..10] -U[i][i+1..i+2]/U[i][i]; [11] (q-p)/U[i][i],
 // where L U is the no-pivot LU of (A - pC)^T.  Vertical: [0..1] -L[c][c-1..c-2];
-// [2] -U[c][c+1]; [3] 1/U[c][c]; [4..7] (D + p'B)^T[c][c+o], o = -2 .. 1.
+// [2] -U[c][c+1]/U[c][c]; [3] 1/U[c][c]; [4..7] (D + p'B)^T[c][c+o], o = -2 .. 1.
 // Factors per column of one vertical matrix (D + qB) and the next apply band:
 //   [0]     -L[c][c-1]
-//   [1..2]  -U[c][c+1], -U[c][c+2]
+//   [1..2]  -U[c][c+1] / U[c][c], -U[c][c+2] / U[c][c]   (pivot folded in)
 //   [3]     1 / U[c][c]
 //   [4..7]  (D + p' B)[c][c+o], o = -1 .. 2      (p' = next radial shift)
 constexpr int ZSTRIDE = 8;
