@@ -18,7 +18,7 @@ independent real matrix equation ("decouple in theta", Section 3).
 """
 import numpy as np
 
-from .sylvester import ModeSystem, BartelsStewart, solve_kron
+from .sylvester import ModeSystem, BartelsStewart, bordered_solve, solve_kron
 from .transforms import slice_wavenumber
 
 
@@ -37,27 +37,63 @@ class _systems(dict):
         return self[k]
 
 
-def poisson(F, slices=None, brute=False):
-    """Coefficients u of -lap u = f for half-complex coefficients F of f."""
+def lifting(bc_vals):
+    """Coefficients of the transfinite (Gordon-Hall) blend of the boundary
+    values of bc_vals ([p][m][n] grid values; only the nodes with j in
+    {0, m-1} or k in {0, n-1} are read): linear in r between the faces
+    r = -1, +1 plus linear in z between z = -1, +1 minus the bilinear corner
+    term.  Its traces on the four faces are the data's interpolants (reading
+    of the unstated boundary conditions: Dirichlet data by lifting)."""
+    from .grid import cheb_points
+    from .transforms import vals2coeffs
+    b = np.asarray(bc_vals, dtype=np.float64)
+    p, m, n = b.shape
+    r = cheb_points(m)[None, :, None]
+    z = cheb_points(n)[None, None, :]
+    lo_r, hi_r = b[:, :1, :], b[:, -1:, :]
+    lo_z, hi_z = b[:, :, :1], b[:, :, -1:]
+    Pr = 0.5 * (1 - r) * lo_r + 0.5 * (1 + r) * hi_r
+    Pz = 0.5 * (1 - z) * lo_z + 0.5 * (1 + z) * hi_z
+    PrPz = (0.25 * (1 - r) * (1 - z) * b[:, :1, :1] + 0.25 * (1 - r) * (1 + z) * b[:, :1, -1:]
+            + 0.25 * (1 + r) * (1 - z) * b[:, -1:, :1] + 0.25 * (1 + r) * (1 + z) * b[:, -1:, -1:])
+    return vals2coeffs(Pr + Pz - PrPz)
+
+
+def poisson(F, slices=None, brute=False, bc=None):
+    """Coefficients u of -lap u = f for half-complex coefficients F of f.
+
+    bc: optional [p][m][n] grid values whose boundary nodes hold the Dirichlet
+    data (consistent at the corners); u = u0 + W with W = lifting(bc) and u0
+    the zero-data solution of the equation with right side corrected by the
+    operator applied to W.  brute=True solves the bordered tau system
+    (boundary rows appended) by dense least squares instead."""
     p, m, n = F.shape
     sys_ = _systems(m, n, p, 'poisson')
     U = np.zeros_like(F)
+    W = lifting(bc) if bc is not None else np.zeros_like(F)
     for s in (range(p) if slices is None else slices):
-        ms, bs = sys_[slice_wavenumber(s, p)]
-        E = ms.rhs(F[s])
+        k = slice_wavenumber(s, p)
+        ms, bs = sys_[k]
+        if brute and bc is not None:
+            U[s] = bordered_solve(m, n, k, 'poisson', None, F[s], W[s])
+            continue
+        E = ms.rhs(F[s]) - ms.full_apply(W[s])
         Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
-        U[s] = ms.expand(Y)
+        U[s] = ms.expand(Y) + W[s]
     return U
 
 
-def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=False):
+def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=False, bc=None):
     """BDF1: X_{n+1} solves eq. HelmholtzMatEqn with delta X = X_n, kappa = dt.
 
     g is either one coefficient array (constant forcing) or an array of
-    shape [nsteps][p][m][n] (g[n] is used by the step n -> n+1)."""
+    shape [nsteps][p][m][n] (g[n] is used by the step n -> n+1).  bc:
+    optional time-constant Dirichlet data as in ``poisson`` (X_{n+1} = S Y S^T
+    + W, the right side corrected by the step operator applied to W)."""
     p, m, n = X0.shape
     kappa = dt
     sys_ = _systems(m, n, p, 'heat', kappa * alpha)
+    W = lifting(bc) if bc is not None else None
     g = np.asarray(g, dtype=np.float64)
     X = np.array(X0, dtype=np.float64, copy=True)
     traj = [X.copy()] if return_all else None
@@ -66,10 +102,16 @@ def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=Fa
         gn = g[step] if g.ndim == 4 else g
         Xn = np.zeros_like(X)
         for s in todo:
-            ms, bs = sys_[slice_wavenumber(s, p)]
+            k = slice_wavenumber(s, p)
+            ms, bs = sys_[k]
+            if W is not None and brute:
+                Xn[s] = bordered_solve(m, n, k, 'heat', kappa * alpha, X[s] + kappa * gn[s], W[s])
+                continue
             E = ms.rhs(X[s] + kappa * gn[s])
+            if W is not None:
+                E = E - ms.full_apply(W[s])
             Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
-            Xn[s] = ms.expand(Y)
+            Xn[s] = ms.expand(Y) + (W[s] if W is not None else 0.0)
         X = Xn
         if return_all:
             traj.append(X.copy())

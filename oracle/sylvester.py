@@ -55,6 +55,13 @@ class ModeSystem:
         self.dA = -Lr
         self.dD = -D2z
         self.m, self.n, self.k = m, n, k
+        # the equation's left operator on a full T-coefficient block (for lifting)
+        Lk_full, C02z, D2z_full = Lk, ops.conv_T_to_C2(n), ops.diff2_T_to_C2(n)
+        if kind == 'poisson':
+            self._full = [(-Pr @ Lk_full, Pz @ C02z), (-Pr @ R2r, Pz @ D2z_full)]
+        else:
+            ka = float(kappa_alpha)
+            self._full = [(Pr @ (R2r - ka * Lk_full), Pz @ C02z), (-ka * Pr @ R2r, Pz @ D2z_full)]
         # right-hand-side map E = P_r R_2 Z C02^T P_z^T, and X = S_r Y S_z^T
         self.rhs_left = Pr @ R2r
         self.rhs_right = (Pz @ ops.conv_T_to_C2(n)).T
@@ -74,6 +81,10 @@ class ModeSystem:
 
     def expand_T(self, X):
         return self.Sr.T @ X @ self.Sz
+
+    def full_apply(self, U):
+        """Left side of the equation on a full T-coefficient block U (m x n)."""
+        return sum(Am @ U @ Bm.T for Am, Bm in self._full)
 
     def apply(self, Y):
         """Left side of the equation: A Y B^T + C Y D^T."""
@@ -137,3 +148,43 @@ class _QZSylv:
             SW[:, j] = S1 @ W[:, j]
             TW[:, j] = T1 @ W[:, j]
         return (self.Z1 @ W @ self.Z2.T).real
+
+
+def bordered_solve(m, n, k, kind, kappa_alpha, rhs_coeffs, wall):
+    """Brute force with boundary data, one slice: the tau equations of the
+    mode (the first m-2 x n-2 C^(2) rows of eq. HelmholtzMatEqn or its
+    Poisson form, acting on the full T-coefficient block U) bordered by the
+    Dirichlet rows  sum_j U[j,:] T_j(+-1) = traces of the data at r = +-1 and
+    sum_k U[:,k] T_k(+-1) = traces at z = +-1.  `wall` is the T-coefficient
+    block of any function with the required boundary traces (its interior
+    does not matter); the bordered system is assembled densely and solved by
+    least squares (it is consistent; the corner rows are redundant).
+
+    rhs_coeffs: Z with right side trunc(R_2 Z C02^T)."""
+    Pr, Pz = ops.tau_rows(m), ops.tau_rows(n)
+    R2r, C02r, C02z = ops.r2_C2(m), ops.conv_T_to_C2(m), ops.conv_T_to_C2(n)
+    Lk = ops.radial_laplacian_r2(m, k)
+    D2z = ops.diff2_T_to_C2(n)
+    if kind == 'poisson':
+        left = [(-Pr @ Lk, Pz @ C02z), (-Pr @ R2r, Pz @ D2z)]
+    else:
+        ka = float(kappa_alpha)
+        left = [(Pr @ (R2r - ka * Lk), Pz @ C02z), (-ka * Pr @ R2r, Pz @ D2z)]
+    # vec(A U B^T) = (B kron A) vec(U), column-major
+    K = sum(np.kron(Bm, Am) for Am, Bm in left)
+    rhs = (Pr @ R2r @ rhs_coeffs @ (Pz @ C02z).T).reshape(-1, order='F')
+    ends_r = np.array([[(-1.0) ** j for j in range(m)], [1.0] * m])   # T_j(-1), T_j(1)
+    ends_z = np.array([[(-1.0) ** j for j in range(n)], [1.0] * n])
+    rows, vals = [], []
+    for e in range(2):       # r = -1, +1: sum_j U[j, kk] T_j(end) for every kk
+        for kk in range(n):
+            Ei = np.zeros((m, n)); Ei[:, kk] = ends_r[e]
+            rows.append(Ei.reshape(-1, order='F')); vals.append(ends_r[e] @ wall[:, kk])
+    for e in range(2):       # z = -1, +1
+        for j in range(m):
+            Ei = np.zeros((m, n)); Ei[j, :] = ends_z[e]
+            rows.append(Ei.reshape(-1, order='F')); vals.append(wall[j, :] @ ends_z[e])
+    Kb = np.vstack([K, np.array(rows)])
+    b = np.concatenate([rhs, np.array(vals)])
+    u = np.linalg.lstsq(Kb, b, rcond=None)[0]
+    return u.reshape((m, n), order='F')
