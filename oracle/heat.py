@@ -118,7 +118,7 @@ def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=Fa
     return (X, traj) if return_all else X
 
 
-def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None):
+def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None, bc=None):
     """Reverse-mode derivatives of L(X_N) for the BDF1 stepping above.
 
     Returns (dL/dX0, dL/dg, dL/dalpha); dL/dg has the shape of g (summed over
@@ -130,13 +130,20 @@ def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None):
     with Sylv(Y) = A Y B^T + C Y D^T, A = C - kappa alpha Lr, D = -kappa alpha D2z.
     Reverse: mu = S^T lam S; Lam = Sylv^-T mu; lam_n = Rhs^T Lam;
     dL/dg_n = kappa lam_n; dL/dalpha += -<Lam, dSylv/dalpha Y_{n+1}>,
-    dSylv/dalpha Y = kappa (dA Y B^T + C Y dD^T)."""
+    dSylv/dalpha Y = kappa (dA Y B^T + C Y dD^T).
+
+    bc: Dirichlet data as in ``heat_steps``.  Then X_{n+1} = S Y S^T + W and
+    the right side carries -Full(W) (Full = the left operator on a full
+    block), so dL/dalpha gains -<Lam, kappa dFull/d(kappa alpha) W> and Y is
+    recovered from X_{n+1} - W; the other derivatives are unchanged (the data
+    enter affinely)."""
     p, m, n = X0.shape
     kappa = dt
     sys_ = _systems(m, n, p, 'heat', kappa * alpha)
     g = np.asarray(g, dtype=np.float64)
     const_g = g.ndim == 3
-    _, traj = heat_steps(X0, g, alpha, dt, nsteps, slices=slices, return_all=True)
+    _, traj = heat_steps(X0, g, alpha, dt, nsteps, slices=slices, return_all=True, bc=bc)
+    W = lifting(bc) if bc is not None else np.zeros_like(X0, dtype=np.float64)
     todo = range(p) if slices is None else slices
     lam = np.array(dL_dXN, dtype=np.float64, copy=True)
     dg = np.zeros_like(g)
@@ -154,9 +161,11 @@ def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None):
                 dg[s] += kappa * w
             else:
                 dg[step, s] = kappa * w
-            Y = np.linalg.lstsq(ms.Sr, np.linalg.lstsq(ms.Sz, Xnext[s].T, rcond=None)[0].T,
+            Y = np.linalg.lstsq(ms.Sr, np.linalg.lstsq(ms.Sz, (Xnext[s] - W[s]).T, rcond=None)[0].T,
                                 rcond=None)[0]
             dS = kappa * (ms.dA @ Y @ ms.B.T + ms.C @ Y @ ms.dD.T)
+            if bc is not None:
+                dS = dS + kappa * ms.full_apply_dka(W[s])
             dalpha -= float(np.sum(Lam * dS))
         lam = lam_prev
     return lam, dg, dalpha

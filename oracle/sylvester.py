@@ -62,6 +62,8 @@ class ModeSystem:
         else:
             ka = float(kappa_alpha)
             self._full = [(Pr @ (R2r - ka * Lk_full), Pz @ C02z), (-ka * Pr @ R2r, Pz @ D2z_full)]
+        # its derivative w.r.t. kappa*alpha (heat; used by the adjoint with lifting)
+        self._dfull = [(-Pr @ Lk_full, Pz @ C02z), (-Pr @ R2r, Pz @ D2z_full)]
         # right-hand-side map E = P_r R_2 Z C02^T P_z^T, and X = S_r Y S_z^T
         self.rhs_left = Pr @ R2r
         self.rhs_right = (Pz @ ops.conv_T_to_C2(n)).T
@@ -85,6 +87,10 @@ class ModeSystem:
     def full_apply(self, U):
         """Left side of the equation on a full T-coefficient block U (m x n)."""
         return sum(Am @ U @ Bm.T for Am, Bm in self._full)
+
+    def full_apply_dka(self, U):
+        """Derivative of ``full_apply(U)`` w.r.t. kappa*alpha (heat)."""
+        return sum(Am @ U @ Bm.T for Am, Bm in self._dfull)
 
     def apply(self, Y):
         """Left side of the equation: A Y B^T + C Y D^T."""

@@ -61,3 +61,33 @@ def test_dense_transpose_of_step_map():
         e = np.zeros(n); e[col] = 1.0
         Phi1[:, col] = heat.heat_steps(e.reshape(X0.shape), zero_g[:1], ALPHA, DT, 1).ravel()
     assert np.allclose(dg[-1].ravel(), DT * (Phi1.T @ c.ravel()), atol=1e-12 * np.abs(Phi1).max())
+
+
+def test_gradients_with_wall_data_match_central_differences():
+    """Run with non-zero Dirichlet data (lifting): dL/dalpha carries the
+    alpha-dependence of the lifted right side; all three gradients against
+    central differences of the lifted forward run."""
+    X0, g, tgt = _problem(3)
+    from oracle import transforms as tr
+    bc = tr.coeffs2vals(inputs.smooth_coeffs(P, M, N, 1.1, np.random.default_rng(9)))
+
+    def loss(X0_, g_, alpha_):
+        XN_ = heat.heat_steps(X0_, g_, alpha_, DT, STEPS, bc=bc)
+        return float(np.sum((XN_ - tgt) ** 2))
+
+    XN = heat.heat_steps(X0, g, ALPHA, DT, STEPS, bc=bc)
+    dX0, dg, dal = heat.heat_adjoint(X0, g, ALPHA, DT, STEPS, 2.0 * (XN - tgt), bc=bc)
+    rng = np.random.default_rng(12)
+    h = 1e-3
+    d = rng.standard_normal(X0.shape)
+    fd = (loss(X0 + h * d, g, ALPHA) - loss(X0 - h * d, g, ALPHA)) / (2 * h)
+    assert abs(fd - float(np.sum(dX0 * d))) <= 1e-7 * abs(fd)
+    d = rng.standard_normal(g.shape)
+    fd = (loss(X0, g + h * d, ALPHA) - loss(X0, g - h * d, ALPHA)) / (2 * h)
+    assert abs(fd - float(np.sum(dg * d))) <= 1e-7 * abs(fd)
+    h = 1e-4 * ALPHA
+    fd = (loss(X0, g, ALPHA + h) - loss(X0, g, ALPHA - h)) / (2 * h)
+    assert abs(fd - dal) <= 1e-7 * abs(fd)
+    # the wall term matters: dropping it changes dL/dalpha
+    _, _, dal0 = heat.heat_adjoint(X0, g, ALPHA, DT, STEPS, 2.0 * (XN - tgt))
+    assert abs(dal0 - dal) > 1e-4 * abs(fd)
