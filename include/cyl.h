@@ -65,6 +65,10 @@ typedef enum {
  * copies, so every bounded device wait runs out (after about 1 ms) and
  * cyl_sync reports CYL_ETIMEOUT; the results of such a plan are garbage. */
 #define CYL_TEST_NO_TMA   32u
+/* allocate the two N-element lifting arrays of non-zero Dirichlet data at
+ * plan time (otherwise the first call with bc != NULL allocates them, which
+ * a stream capture does not allow) */
+#define CYL_WITH_BC       64u
 
 /* space selector of cyl_poisson */
 #define CYL_VALUES 0
@@ -82,7 +86,7 @@ typedef enum {
  *   adi_tol    in (0, 1e-2]: target relative accuracy of the Zolotarev bound;
  *              the iteration count per mode is J = ceil(log(16 gamma) log(4/tol) / pi^2).
  *   flags      CYL_WITH_POISSON and/or CYL_WITH_HEAT, optionally
- *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL.
+ *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL, CYL_WITH_BC.
  *   stream     cudaStream_t on which every device call of this plan runs
  *              (NULL = legacy default stream).  Ignored with CYL_HOST_ONLY.
  *
@@ -109,13 +113,30 @@ cyl_status cyl_vals2coeffs(cyl_plan_t plan, const double *vals, double *coeffs);
 cyl_status cyl_coeffs2vals(cyl_plan_t plan, const double *coeffs, double *vals);
 
 /*
- * cyl_poisson -- solve -lap u = f, zero Dirichlet data (the Poisson solves of
- * Section 4, with the Section 3 discretisation without its identity term).
- * f and u are device arrays of N float64; space = CYL_VALUES (both are grid
- * values) or CYL_COEFFS (both are half-complex coefficients).  f and u may
- * alias.  Needs CYL_WITH_POISSON.
+ * Dirichlet data (bc arguments).  The paper's problem statement (Section 1)
+ * poses the wall condition u = 0; non-zero data are applied by lifting:
+ * u = u0 + W, where W is the transfinite blend of the data (linear in r
+ * between the faces r = -1, +1 of the doubled grid, plus linear in z between
+ * z = -1, +1, minus the bilinear corner term), u0 has zero data and solves
+ * the same equation with the left operator applied to W moved to the right
+ * side.  bc is a device array of N float64 GRID VALUES in the [p][m][n]
+ * layout of which only the boundary nodes (radial index 0 or m-1, vertical
+ * index 0 or n-1) are read; the interior is ignored.  Without
+ * CYL_BOTH_PARITIES the data must be a field on the doubled grid
+ * (value at (-r, z, theta) = value at (r, z, theta + pi)), as f must.
+ * bc = NULL means zero data.  The first call with bc != NULL allocates two
+ * N-element plan arrays unless the plan was made with CYL_WITH_BC.
  */
-cyl_status cyl_poisson(cyl_plan_t plan, const double *f, double *u, int space);
+
+/*
+ * cyl_poisson -- solve -lap u = f with Dirichlet data bc (the Poisson solves
+ * of Section 4, with the Section 3 discretisation without its identity
+ * term).  f and u are device arrays of N float64; space = CYL_VALUES (both
+ * are grid values) or CYL_COEFFS (both are half-complex coefficients); bc is
+ * NULL (u = 0 on the wall) or grid values as described above, in either
+ * space.  f and u may alias.  Needs CYL_WITH_POISSON.
+ */
+cyl_status cyl_poisson(cyl_plan_t plan, const double *f, const double *bc, double *u, int space);
 
 /*
  * cyl_heat_step -- advance (d_t - alpha lap) T = g by nsteps BDF1 steps
@@ -133,6 +154,12 @@ cyl_status cyl_poisson(cyl_plan_t plan, const double *f, double *u, int space);
  */
 cyl_status cyl_heat_step(cyl_plan_t plan, double *T, const double *g, long long g_step_stride,
                          int nsteps, double *ckpt, int ckpt_every);
+
+/* cyl_heat_step_bc -- cyl_heat_step with time-constant Dirichlet data bc
+ * (grid values, see above; NULL = zero data): every step returns
+ * T_{n+1} = u0 + W with u0 of zero data.  T_0 itself need not meet the data. */
+cyl_status cyl_heat_step_bc(cyl_plan_t plan, double *T, const double *g, long long g_step_stride,
+                            int nsteps, const double *bc, double *ckpt, int ckpt_every);
 
 /*
  * cyl_heat_adjoint -- reverse-mode derivatives of a scalar loss L(T_N) of the
@@ -163,6 +190,15 @@ cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
                             long long g_step_stride, int nsteps, int ckpt_every,
                             const double *dL_dTN, double *dL_dT0, double *dL_dg,
                             double *dL_dalpha, void *workspace, size_t workspace_bytes);
+
+/* cyl_heat_adjoint_bc -- cyl_heat_adjoint of the run cyl_heat_step_bc(T0, g,
+ * g_step_stride, nsteps, bc) computes.  The data enter that run affinely, so
+ * dL/dT0 and dL/dg are those of the zero-data run; the alpha identity holds
+ * on the lifted states, which the recomputation produces with bc. */
+cyl_status cyl_heat_adjoint_bc(cyl_plan_t plan, const double *T0, const double *g,
+                               long long g_step_stride, int nsteps, const double *bc, int ckpt_every,
+                               const double *dL_dTN, double *dL_dT0, double *dL_dg,
+                               double *dL_dalpha, void *workspace, size_t workspace_bytes);
 
 /* Bytes of device workspace cyl_heat_adjoint needs (0 when need_alpha is 0). */
 cyl_status cyl_heat_adjoint_workspace(cyl_plan_t plan, int nsteps, int ckpt_every, int need_alpha,

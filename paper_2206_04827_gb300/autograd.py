@@ -6,9 +6,11 @@ passes run in libcyl's CUDA kernels.
 
 T0: [p][m][n] float64 CUDA coefficients (half-complex, see include/cyl.h);
 g: one coefficient array (constant forcing) or [nsteps][p][m][n] (g[n] drives
-step n -> n+1); alpha: 0-dim float64 tensor.  Gradients flow to T0, g and
-alpha.  Plans are cached per (grid, alpha, dt, tolerance); a new alpha builds
-a new plan on the host.
+step n -> n+1); alpha: 0-dim float64 tensor; bc: None (zero wall data) or
+grid values whose boundary nodes hold time-constant Dirichlet data (no
+gradient flows to bc).  Gradients flow to T0, g and alpha.  Plans are
+cached per (grid, alpha, dt, tolerance); a new alpha builds a new plan on
+the host.
 """
 import torch
 
@@ -31,33 +33,35 @@ def plan_for(m, n, p, alpha, dt, tol):
 
 class HeatRun(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, T0, g, alpha, dt, nsteps, ckpt_every, tol):
+    def forward(ctx, T0, g, alpha, dt, nsteps, ckpt_every, tol, bc):
         p, m, n = T0.shape
         plan = plan_for(m, n, p, alpha.item(), dt, tol)
         T0c = T0.contiguous()
         gc = g.contiguous() if g is not None else None
         stride = 0 if (gc is None or gc.dim() == 3) else p * m * n
+        bcc = bc.contiguous() if bc is not None else None
         T = T0c.clone()
-        plan.heat_step(T, gc, nsteps, g_step_stride=stride)
-        ctx.save_for_backward(T0c, gc if gc is not None else torch.empty(0, device=T0.device))
-        ctx.meta = (plan, nsteps, ckpt_every, stride, g is not None)
+        plan.heat_step(T, gc, nsteps, g_step_stride=stride, bc=bcc)
+        empty = torch.empty(0, device=T0.device)
+        ctx.save_for_backward(T0c, gc if gc is not None else empty, bcc if bcc is not None else empty)
+        ctx.meta = (plan, nsteps, ckpt_every, stride, g is not None, bc is not None)
         return T
 
     @staticmethod
     def backward(ctx, dT):
-        T0, gsaved = ctx.saved_tensors
-        plan, nsteps, ckpt_every, stride, has_g = ctx.meta
+        T0, gsaved, bcsaved = ctx.saved_tensors
+        plan, nsteps, ckpt_every, stride, has_g, has_bc = ctx.meta
         g = gsaved if has_g else None
         dT0 = torch.empty_like(T0)
         dg = torch.empty_like(g) if (has_g and ctx.needs_input_grad[1]) else None
         dal = torch.zeros(1, dtype=torch.float64, device=T0.device) if ctx.needs_input_grad[2] else None
         plan.heat_adjoint(T0, g, nsteps, dT.contiguous(), dT0, dg, dal, g_step_stride=stride,
-                          ckpt_every=ckpt_every)
-        return (dT0, dg, dal.reshape(()) if dal is not None else None, None, None, None, None)
+                          ckpt_every=ckpt_every, bc=bcsaved if has_bc else None)
+        return (dT0, dg, dal.reshape(()) if dal is not None else None, None, None, None, None, None)
 
 
-def heat(T0, g, alpha, dt, nsteps, ckpt_every=None, tol=1e-14):
+def heat(T0, g, alpha, dt, nsteps, ckpt_every=None, tol=1e-14, bc=None):
     """Differentiable BDF1 run; see the module docstring."""
     if not torch.is_tensor(alpha):
         alpha = torch.tensor(float(alpha), dtype=torch.float64, device=T0.device)
-    return HeatRun.apply(T0, g, alpha, float(dt), int(nsteps), int(ckpt_every or nsteps), tol)
+    return HeatRun.apply(T0, g, alpha, float(dt), int(nsteps), int(ckpt_every or nsteps), tol, bc)

@@ -50,6 +50,8 @@ struct cyl_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *d_err = nullptr;         // device status word written by bounded waits
   double *d_apart = nullptr;    // per-item partial sums of the alpha gradient
+  double *d_lift = nullptr;     // coefficients of the lifting W of the boundary data
+  double *d_corr = nullptr;     // right-side correction of the lifted problem
   size_t N = 0;
 };
 
@@ -89,6 +91,8 @@ void free_device(cyl_plan_s *P) {
   for (auto &p : P->d_tmp) cudaFree(p);
   cudaFree(P->d_err);
   cudaFree(P->d_apart);
+  cudaFree(P->d_lift);
+  cudaFree(P->d_corr);
 }
 
 cyl_status from_cuda(cudaError_t e) {
@@ -142,8 +146,26 @@ cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
   return a;
 }
 
+// Boundary data by lifting: W = coefficients of the blend of bc's boundary
+// nodes (into d_lift) and the right-side correction of the kind's equation
+// applied to W (into d_corr).  Uses d_tmp[0], d_tmp[1] as transform scratch.
+cyl_status prepare_lift(cyl_plan_s *P, int kind, const double *bc) {
+  cudaError_t e = cudaSuccess;
+  if (!P->d_lift) e = cudaMalloc((void **)&P->d_lift, P->N * sizeof(double));
+  if (e == cudaSuccess && !P->d_corr) e = cudaMalloc((void **)&P->d_corr, P->N * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return from_cuda(e);
+  }
+  cyl::AdiArgs a = adi_args(P, kind);
+  const double c0 = kind == 1 ? 1.0 : 0.0;
+  const double c1 = kind == 1 ? P->hp.alpha * P->hp.dt : 1.0;
+  return from_cuda(cyl::launch_lift(a, bc, P->d_corr, P->d_lift, P->d_corr, c0, c1, P->d_W[4], P->d_W[0],
+                                    P->d_W[2], P->d_tmp[0], P->d_tmp[1], std::min(P->threads[kind], 256), P->st));
+}
+
 cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
-                   long long gstride, int nsteps, double *ckpt, int ckpt_every) {
+                   long long gstride, int nsteps, double *ckpt, int ckpt_every, bool lifted = false) {
   cyl::AdiArgs a{};
   a.items = P->d_items[kind];
   a.nitems = P->nitems[kind];
@@ -171,6 +193,8 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   a.err = P->d_err;
   a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
   a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
+  a.lift = lifted ? P->d_lift : nullptr;
+  a.corr = lifted ? P->d_corr : nullptr;
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
@@ -319,7 +343,7 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
   if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT))) return CYL_EINVAL;
   if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL |
-                          CYL_TEST_NO_TMA))
+                          CYL_TEST_NO_TMA | CYL_WITH_BC))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if ((long long)n_r * n_z * n_theta > (1LL << 40)) return CYL_EINVAL;
@@ -382,6 +406,8 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_apart, std::max(1, P->nitems[1]) * sizeof(double));
+  if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_lift, P->N * sizeof(double));
+  if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_corr, P->N * sizeof(double));
   if (e == cudaSuccess && !(P->use_smem[0] == 2 && P->use_smem[1] == 2)) {
     P->gwork_per_item = ((long long)P->smem_rows * P->ld + (long long)P->maxM * P->ld + 31) / 32 * 32;
     const int maxItems = std::max(P->nitems[0], P->nitems[1]);
@@ -416,19 +442,28 @@ cyl_status cyl_coeffs2vals(cyl_plan_t P, const double *coeffs, double *vals) {
   return coeffs2vals_impl(P, coeffs, vals);
 }
 
-cyl_status cyl_poisson(cyl_plan_t P, const double *f, double *u, int space) {
+cyl_status cyl_poisson(cyl_plan_t P, const double *f, const double *bc, double *u, int space) {
   if (!P || !f || !u || (space != CYL_VALUES && space != CYL_COEFFS)) return CYL_EINVAL;
   if (P->host_only || P->is_batch || !P->hp.kind[0].built) return CYL_ESTATE;
-  if (space == CYL_COEFFS) return run_adi(P, 0, f, u, nullptr, 0.0, 0, 1, nullptr, 1);
-  cyl_status s = vals2coeffs_impl(P, f, P->d_tmp[2]);
-  if (s != CYL_OK) return s;
-  s = run_adi(P, 0, P->d_tmp[2], P->d_tmp[2], nullptr, 0.0, 0, 1, nullptr, 1);
-  if (s != CYL_OK) return s;
-  return coeffs2vals_impl(P, P->d_tmp[2], u);
+  const double *F = f;
+  cyl_status s;
+  if (space == CYL_VALUES) {
+    if ((s = vals2coeffs_impl(P, f, P->d_tmp[2])) != CYL_OK) return s;
+    F = P->d_tmp[2];
+  }
+  if (bc && (s = prepare_lift(P, 0, bc)) != CYL_OK) return s;
+  double *U = space == CYL_VALUES ? P->d_tmp[2] : u;
+  if ((s = run_adi(P, 0, F, U, nullptr, 0.0, 0, 1, nullptr, 1, bc != nullptr)) != CYL_OK) return s;
+  return space == CYL_VALUES ? coeffs2vals_impl(P, P->d_tmp[2], u) : CYL_OK;
 }
 
 cyl_status cyl_heat_step(cyl_plan_t P, double *T, const double *g, long long g_step_stride, int nsteps,
                          double *ckpt, int ckpt_every) {
+  return cyl_heat_step_bc(P, T, g, g_step_stride, nsteps, nullptr, ckpt, ckpt_every);
+}
+
+cyl_status cyl_heat_step_bc(cyl_plan_t P, double *T, const double *g, long long g_step_stride, int nsteps,
+                            const double *bc, double *ckpt, int ckpt_every) {
   if (!P || !T || nsteps < 0 || g_step_stride < 0) return CYL_EINVAL;
   if (P->is_batch) return CYL_ESTATE;
   if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
@@ -439,7 +474,11 @@ cyl_status cyl_heat_step(cyl_plan_t P, double *T, const double *g, long long g_s
     cudaError_t e = cudaMemcpyAsync(ckpt, T, P->N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
     if (e != cudaSuccess) return from_cuda(e);
   }
-  return run_adi(P, 1, T, T, g, P->hp.dt, g ? g_step_stride : 0, nsteps, ckpt, ckpt_every);
+  if (bc) {
+    cyl_status s = prepare_lift(P, 1, bc);
+    if (s != CYL_OK) return s;
+  }
+  return run_adi(P, 1, T, T, g, P->hp.dt, g ? g_step_stride : 0, nsteps, ckpt, ckpt_every, bc != nullptr);
 }
 
 static size_t adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, bool need_alpha) {
@@ -459,6 +498,14 @@ cyl_status cyl_heat_adjoint_workspace(cyl_plan_t P, int nsteps, int ckpt_every, 
 cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, long long g_step_stride, int nsteps,
                             int ckpt_every, const double *dL_dTN, double *dL_dT0, double *dL_dg,
                             double *dL_dalpha, void *workspace, size_t workspace_bytes) {
+  return cyl_heat_adjoint_bc(P, T0, g, g_step_stride, nsteps, nullptr, ckpt_every, dL_dTN, dL_dT0, dL_dg,
+                             dL_dalpha, workspace, workspace_bytes);
+}
+
+cyl_status cyl_heat_adjoint_bc(cyl_plan_t P, const double *T0, const double *g, long long g_step_stride,
+                               int nsteps, const double *bc, int ckpt_every, const double *dL_dTN,
+                               double *dL_dT0, double *dL_dg, double *dL_dalpha, void *workspace,
+                               size_t workspace_bytes) {
   if (!P || !dL_dTN || !dL_dT0 || nsteps < 0 || ckpt_every < 1 || g_step_stride < 0) return CYL_EINVAL;
   if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
   if (dL_dalpha && !T0) return CYL_EINVAL;
@@ -498,8 +545,11 @@ cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, lon
   e = cudaMemcpyAsync(ck, T0, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
   if (e != cudaSuccess) return from_cuda(e);
   cyl_status s;
+  // the data enter the run affinely: only the recomputed states see them
+  if (bc && (s = prepare_lift(P, 1, bc)) != CYL_OK) return s;
+  const bool lifted = bc != nullptr;
   if (nseg > 1) {                                       // checkpoints X_c, X_2c, ... (ck slot s = X_{s c})
-    s = run_adi(P, 1, T0, work, g, kappa, g ? g_step_stride : 0, (nseg - 1) * c, ck, c);
+    s = run_adi(P, 1, T0, work, g, kappa, g ? g_step_stride : 0, (nseg - 1) * c, ck, c, lifted);
     if (s != CYL_OK) return s;
   }
   adj.traj = seg;
@@ -509,7 +559,7 @@ cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, lon
     e = cudaMemcpyAsync(seg, ck + (size_t)sgi * N, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
     if (e != cudaSuccess) return from_cuda(e);
     const double *gseg = g ? g + (size_t)n_lo * g_step_stride : nullptr;
-    s = run_adi(P, 1, seg, work, gseg, kappa, g ? g_step_stride : 0, n_hi - n_lo, seg, 1);
+    s = run_adi(P, 1, seg, work, gseg, kappa, g ? g_step_stride : 0, n_hi - n_lo, seg, 1, lifted);
     if (s != CYL_OK) return s;
     adj.n_lo = n_lo;
     adj.n_hi = n_hi;
@@ -676,6 +726,7 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
     fac.insert(fac.end(), hps[i].factors.begin(), hps[i].factors.end());
     for (Item it : hps[i].kind[1].items) {
       it.roff += base; it.zoff += base; it.r2off += base; it.c02off += base;
+      it.lkoff += base; it.d2off += base;
       if (it.roffT >= 0) it.roffT += base;
       if (it.zoffT >= 0) it.zoffT += base;
       it.xoff = P->offsets[i];

@@ -19,6 +19,8 @@
 // the radial phase and one row in the vertical phase.
 #include <cstdio>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace cyl {
@@ -350,6 +352,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
   if (tid == 0 && !a.test_no_tma) issue_tables<false>(sh, a, it, c0, c0);
   const double *Xsrc = a.Xin + it.xoff;
   double *Xout = a.Xout + it.xoff;
+  const double *lift = a.lift ? a.lift + it.xoff : nullptr;
   const double *Gbase = a.G ? a.G + it.xoff : nullptr;
   for (int step = 0; step < a.nsteps; ++step) {
     const double *Gs = Gbase ? Gbase + (size_t)step * a.gstride : nullptr;
@@ -373,6 +376,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
       S[ap * ld + cc] = acc;
     }
     gp.sync();
+    const double *corr = a.corr ? a.corr + it.xoff : nullptr;
     for (int e = tid; e < M * W; e += nth) {
       const int aa = e / W, cc = e - aa * W;
       double acc = 0.0;
@@ -380,6 +384,10 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
       for (int s = -1; s <= 3; ++s) {
         const int q = aa + s;
         if (q >= 0 && q < it.Mfull) acc = fma(r2[aa * R2STRIDE + s + 1], S[q * ld + cc], acc);
+      }
+      if (corr) {
+        const int sl = cc / Nz, b = cc - sl * Nz;
+        acc += corr[(size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * aa) * n + it.pz + 2 * b];
       }
       Fa[aa * ld + cc] = acc;
     }
@@ -402,6 +410,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
       if (r1 && c0b) x -= Ys[ap * ld + b - 1];
       if (r1 && c1) x += Ys[ap * ld + b];
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * ap) * n + it.pz + 2 * b;
+      if (lift) x += lift[o];
       Xout[o] = x;
       if (ck) ck[o] = x;
     }
@@ -411,8 +420,9 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
         const int ap = e / Wf, cc = e - ap * Wf;
         const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
         const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(po + 2 * ap) * n + it.pz + 2 * b;
-        Xout[o] = 0.0;
-        if (ck) ck[o] = 0.0;
+        const double x = lift ? lift[o] : 0.0;
+        Xout[o] = x;
+        if (ck) ck[o] = x;
       }
     }
     gp.sync();
@@ -625,6 +635,92 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
     }
   }
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+// Dirichlet data by lifting (reading of the unstated boundary conditions):
+// W = transfinite blend of the boundary nodes of bc (linear in r between the
+// faces r = -1, +1, plus linear in z between z = -1, +1, minus the bilinear
+// corner term), evaluated on every grid node.
+__global__ void lift_values_kernel(const double *__restrict__ bc, double *__restrict__ Wv, int p, int m, int n) {
+  const long long total = (long long)p * m * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % n);
+    const int j = (int)((e / n) % m);
+    const long long l = e / ((long long)m * n);
+    const double r = cospi((double)(m - 1 - j) / (double)(m - 1));
+    const double z = cospi((double)(n - 1 - k) / (double)(n - 1));
+    const double *B = bc + l * m * n;
+    const double r0 = B[(size_t)0 * n + k], r1 = B[(size_t)(m - 1) * n + k];
+    const double z0 = B[(size_t)j * n + 0], z1 = B[(size_t)j * n + n - 1];
+    const double c00 = B[0], c01 = B[n - 1], c10 = B[(size_t)(m - 1) * n], c11 = B[(size_t)(m - 1) * n + n - 1];
+    const double pr = 0.5 * (1.0 - r) * r0 + 0.5 * (1.0 + r) * r1;
+    const double pz = 0.5 * (1.0 - z) * z0 + 0.5 * (1.0 + z) * z1;
+    const double prz = 0.25 * ((1.0 - r) * (1.0 - z) * c00 + (1.0 - r) * (1.0 + z) * c01 +
+                               (1.0 + r) * (1.0 - z) * c10 + (1.0 + r) * (1.0 + z) * c11);
+    Wv[e] = pr + pz - prz;
+  }
+}
+
+// Right-side correction of the lifted problem on every item's class block:
+// corr = c1 (L_k W C02^T + R_2 W D2^T) - c0 R_2 W C02^T (tau rows), i.e. minus
+// the left operator of the step (c0 = 1, c1 = kappa alpha) or of the Poisson
+// problem (c0 = 0, c1 = 1) applied to W.  One CTA per item.
+__global__ void lift_correction_kernel(const AdiArgs a, const double *__restrict__ Wc, double *__restrict__ corr,
+                                       double c0, double c1) {
+  const Item it = a.items[blockIdx.x];
+  const int m = it.m, n = it.n, M = it.M, Nz = it.Nz, nsl = it.nsl;
+  const long long slice = (long long)m * n;
+  const double *r2 = a.fac + it.r2off, *c02 = a.fac + it.c02off, *lk = a.fac + it.lkoff, *d2 = a.fac + it.d2off;
+  const double *Wb = Wc + it.xoff;
+  double *Cb = corr + it.xoff;
+  for (int e = threadIdx.x; e < M * nsl * Nz; e += blockDim.x) {
+    const int aa = e / (nsl * Nz), cc = e - aa * (nsl * Nz);
+    const int sl = cc / Nz, b = cc - sl * Nz;
+    const int i = it.pr + 2 * aa, j = it.pz + 2 * b;
+    const double *Ws = Wb + (size_t)(it.s0 + sl) * slice;
+    // row-wise z passes of W at radial class row q: (W C02^T)[q][j], (W D2^T)[q][j]
+    auto zc = [&](int q) {
+      const double *row = Ws + (size_t)(it.pr + 2 * q) * n;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (j + 2 * t < n) s = fma(c02[b * C02STRIDE + t], row[j + 2 * t], s);
+      return s;
+    };
+    auto zd = [&](int q) {
+      const double *row = Ws + (size_t)(it.pr + 2 * q) * n;
+      return (j + 2 < n) ? d2[b] * row[j + 2] : 0.0;
+    };
+    double acc = 0.0;
+#pragma unroll
+    for (int s = -1; s <= 3; ++s) {       // R_2 (c1 W D2^T - c0 W C02^T)
+      const int q = aa + s;
+      if (q >= 0 && q < it.Mfull) acc = fma(r2[aa * R2STRIDE + s + 1], c1 * zd(q) - c0 * zc(q), acc);
+    }
+#pragma unroll
+    for (int t = 0; t <= 2; ++t) {        // c1 L_k W C02^T
+      const int q = aa + t;
+      if (q < it.Mfull) acc = fma(c1 * lk[aa * 3 + t], zc(q), acc);
+    }
+    Cb[(size_t)(it.s0 + sl) * slice + (size_t)i * n + j] = acc;
+  }
+}
+
+cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
+                        double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
+                        int threads, cudaStream_t st) {
+  const long long N = (long long)a.p * a.m * a.n;
+  lift_values_kernel<<<(int)std::min<long long>((N + 255) / 256, 152LL * 16), 256, 0, st>>>(bc, Wv, a.p, a.m, a.n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // values -> coefficients of W (the same three axis transforms as cyl_vals2coeffs)
+  if ((e = launch_axis_matvec(Wv, tmp0, Wz, (long long)a.p * a.m, a.n, 1, st)) != cudaSuccess) return e;
+  if ((e = launch_axis_matvec(tmp0, tmp1, Wr, a.p, a.m, a.n, st)) != cudaSuccess) return e;
+  if ((e = launch_axis_matvec(tmp1, Wc_out, Wt, 1, a.p, (long long)a.m * a.n, st)) != cudaSuccess) return e;
+  // corr is written (and later read) only at the items' class positions
+  lift_correction_kernel<<<a.nitems, threads, 0, st>>>(a, Wc_out, corr, c0, c1);
+  return cudaGetLastError();
 }
 
 __global__ void sum_partials_kernel(const double *part, int n, double scale, double *out) {

@@ -32,6 +32,8 @@ struct AdiArgs {
   int *err;                // device status word (CYL_ERR_TIMEOUT on a bounded-wait timeout)
   long long group_doubles; // batch kernel: shared-memory slice per thread group (multiple of 32)
   long long wait_limit;    // SM clock cycles a bounded wait may spin (about 1 s normally)
+  const double *lift;      // coefficients of the lifting W of the boundary data, or NULL
+  const double *corr;      // right-side correction of the lifted problem (class positions), or NULL
   int test_no_tma;         // failure-detection test: never start table copies, so waits run out
 };
 
@@ -51,6 +53,9 @@ struct AdjointArgs {
 };
 
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
+                        double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
+                        int threads, cudaStream_t st);
 cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st);
 
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level);

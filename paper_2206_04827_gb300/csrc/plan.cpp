@@ -406,7 +406,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
   hp.factors.clear();
   auto &F = hp.factors;
   // right-hand-side bands, shared by both kinds
-  long long r2off[2] = {0, 0}, c02off[2] = {0, 0};
+  long long r2off[2] = {0, 0}, c02off[2] = {0, 0}, d2off[2] = {0, 0};
   {
     Band R2 = full_R2(m), C02 = full_C02(n);
     for (int pr = 0; pr < 2; ++pr) {
@@ -427,7 +427,30 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
         }
       if (F.size() & 1) F.push_back(0.0);
     }
+    Band D2z = op_D2(n);   // D2[j][j+2] (lifting correction)
+    for (int pz = 0; pz < 2; ++pz) {
+      d2off[pz] = (long long)F.size();
+      for (int b = 0; b < hp.Nc[pz]; ++b) {
+        const int i = pz + 2 * b;
+        F.push_back(i + 2 < n ? D2z.get(i, i + 2) : 0.0);
+      }
+      if (F.size() & 1) F.push_back(0.0);
+    }
   }
+  // radial operator L_k = R C12 D1 + R^2 D2 - k^2 C02 per (k, class): L_k[i][i+2t], t = 0..2
+  std::vector<long long> lkoff((h + 1) * 2, -1);
+  for (int k = 0; k <= h; ++k)
+    for (int pr = 0; pr < 2; ++pr) {
+      if (hp.Mc[pr] == 0 || (!both && pr != (k & 1))) continue;
+      Band Lf = full_L(m, k);
+      lkoff[k * 2 + pr] = (long long)F.size();
+      for (int a = 0; a < hp.Mc[pr]; ++a)
+        for (int t = 0; t <= 2; ++t) {
+          const int i = pr + 2 * a, j = i + 2 * t;
+          F.push_back(j < m ? Lf.get(i, j) : 0.0);
+        }
+      if (F.size() & 1) F.push_back(0.0);
+    }
 
   for (int kind = 0; kind < 2; ++kind) {
     KindTables &KT = hp.kind[kind];
@@ -536,6 +559,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             it.J = S.J; it.roff = roff; it.zoff = zoff; it.r2off = r2off[pr]; it.c02off = c02off[pz];
             it.roffT = roffT; it.zoffT = zoffT;
             it.m = m; it.n = n; it.xoff = 0;
+            it.lkoff = lkoff[k * 2 + pr]; it.d2off = d2off[pz];
             KT.items.push_back(it);
           };
           if (k == 0) add_item(0, 1);

@@ -67,6 +67,8 @@ struct Item {
   long long c02off;   // offset of the C02 band table   [Nz][C02STRIDE]
   long long roffT;    // transposed radial factors (adjoint), heat only, else -1
   long long zoffT;    // transposed vertical factors (adjoint), heat only, else -1
+  long long lkoff;    // radial operator L_k bands [M][3] (lifting of boundary data)
+  long long d2off;    // vertical D2 band [Nz] (lifting of boundary data)
 };
 
 struct Shifts {

@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # status codes and flags (include/cyl.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
-WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA = 1, 2, 4, 8, 16, 32
+WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA, WITH_BC = 1, 2, 4, 8, 16, 32, 64
 VALUES, COEFFS = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -33,10 +33,13 @@ _sig = {
     'cyl_destroy': (ctypes.c_int, [_vp]),
     'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
     'cyl_coeffs2vals': (ctypes.c_int, [_vp, _vp, _vp]),
-    'cyl_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    'cyl_poisson': (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int]),
     'cyl_heat_step': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int]),
+    'cyl_heat_step_bc': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     'cyl_heat_adjoint': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp, _vp, _vp, ctypes.c_size_t]),
+    'cyl_heat_adjoint_bc': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                           _vp, _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_size_t)]),
     'cyl_status_string': (ctypes.c_char_p, [ctypes.c_int]),
@@ -144,14 +147,18 @@ class Plan:
                'cyl_coeffs2vals')
         return vals
 
-    def poisson(self, f, u, space=COEFFS):
-        _check(_lib.cyl_poisson(self._h, _ptr(f, 'f', self.N), _ptr(u, 'u', self.N), int(space)), 'cyl_poisson')
+    def poisson(self, f, u, space=COEFFS, bc=None):
+        """-lap u = f; bc: None (zero wall data) or grid values whose boundary
+        nodes hold the Dirichlet data (include/cyl.h: cyl_poisson)."""
+        _check(_lib.cyl_poisson(self._h, _ptr(f, 'f', self.N), _ptr(bc, 'bc', self.N), _ptr(u, 'u', self.N),
+                                int(space)), 'cyl_poisson')
         return u
 
-    def heat_step(self, T, g=None, nsteps=1, g_step_stride=0, ckpt=None, ckpt_every=1):
+    def heat_step(self, T, g=None, nsteps=1, g_step_stride=0, ckpt=None, ckpt_every=1, bc=None):
         need = None if ckpt is None else (nsteps // ckpt_every + 1) * self.N
-        _check(_lib.cyl_heat_step(self._h, _ptr(T, 'T', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
-                                  int(nsteps), _ptr(ckpt, 'ckpt', need), int(ckpt_every)), 'cyl_heat_step')
+        _check(_lib.cyl_heat_step_bc(self._h, _ptr(T, 'T', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
+                                     int(nsteps), _ptr(bc, 'bc', self.N), _ptr(ckpt, 'ckpt', need),
+                                     int(ckpt_every)), 'cyl_heat_step_bc')
         return T
 
     def adjoint_workspace_bytes(self, nsteps, ckpt_every, need_alpha):
@@ -161,19 +168,19 @@ class Plan:
         return nb.value
 
     def heat_adjoint(self, T0, g, nsteps, dL_dTN, dL_dT0, dL_dg=None, dL_dalpha=None, g_step_stride=0,
-                     ckpt_every=1, workspace=None):
+                     ckpt_every=1, workspace=None, bc=None):
         """Reverse-mode gradients of the BDF1 run (see include/cyl.h: cyl_heat_adjoint).
         The workspace tensor is allocated here (torch) when not given."""
         nbytes = self.adjoint_workspace_bytes(nsteps, ckpt_every, dL_dalpha is not None)
         if nbytes and workspace is None:
             import torch
             workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=dL_dT0.device)
-        _check(_lib.cyl_heat_adjoint(self._h, _ptr(T0, 'T0', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
-                                     int(nsteps), int(ckpt_every), _ptr(dL_dTN, 'dL_dTN', self.N),
+        _check(_lib.cyl_heat_adjoint_bc(self._h, _ptr(T0, 'T0', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
+                                     int(nsteps), _ptr(bc, 'bc', self.N), int(ckpt_every), _ptr(dL_dTN, 'dL_dTN', self.N),
                                      _ptr(dL_dT0, 'dL_dT0', self.N), _ptr(dL_dg, 'dL_dg', self.N),
                                      _ptr(dL_dalpha, 'dL_dalpha', 1),
                                      _ptr(workspace, 'workspace', (nbytes + 7) // 8) if nbytes else None,
-                                     ctypes.c_size_t(nbytes)), 'cyl_heat_adjoint')
+                                     ctypes.c_size_t(nbytes)), 'cyl_heat_adjoint_bc')
         return dL_dT0
 
     def sync(self):
