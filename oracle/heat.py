@@ -11,11 +11,20 @@ independent real matrix equation ("decouple in theta", Section 3).
                      forcing of step n -> n+1 taken at level n (the
                      extrapolation g(t+h) ~ g(t) stated beside eq.
                      HelmholtzMatEqn).
+* ``bdf_coefficients`` / ``heat_bdf`` -- the b-th order BDF of Section 3
+                     (BDF 4 printed; delta^(b) defined by sampling at t, t-h,
+                     ... and taking differences): kappa^(b) and delta^(b) from
+                     the backward-difference form, the first steps of a run
+                     through lower orders while fewer than b past states are
+                     known (reading: start-up is unstated).
 * ``heat_adjoint``-- gradients of a scalar loss of X_N with respect to X_0,
                      every g_n and alpha, by the chain rule through the
                      direct solves (no part of the paper; the transpose of
                      the stepping map above).
 """
+from fractions import Fraction
+from math import comb
+
 import numpy as np
 
 from .sylvester import ModeSystem, BartelsStewart, bordered_solve, solve_kron
@@ -116,6 +125,72 @@ def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=Fa
         if return_all:
             traj.append(X.copy())
     return (X, traj) if return_all else X
+
+
+def bdf_coefficients(b):
+    """(kappa^(b) / h, [beta_0 .. beta_{b-1}]) as exact fractions for the
+    b-th order BDF  y_{n+1} - kappa y'_{n+1} = sum_i beta_i y_{n-i}.
+
+    Definition used: the backward-difference form sum_{j=1..b} (1/j) nabla^j
+    y_{n+1} = h y'_{n+1} with nabla y_{n+1} = y_{n+1} - y_n (the differences of
+    the samples at t+h, t, t-h, ...), divided by its coefficient of y_{n+1}."""
+    if not 1 <= b <= 6:
+        raise ValueError('BDF order must be 1..6')
+    # coefficient of y_{n+1-i} in sum_j (1/j) nabla^j y_{n+1}
+    a = [sum(Fraction((-1) ** i * comb(j, i), j) for j in range(max(i, 1), b + 1)) for i in range(b + 1)]
+    return 1 / a[0], [-a[i] / a[0] for i in range(1, b + 1)]
+
+
+def heat_bdf(hist, g, alpha, dt, order, nsteps, nvalid=None, slices=None, brute=False, bc=None,
+             return_all=False):
+    """The b-th order BDF run (b = order) of eq. HelmholtzMatEqn:
+    (R_2 - kappa alpha L) X_{n+1} C02^T - kappa alpha R_2 X_{n+1} D2^T
+        = R_2 (delta^(b) X_n + kappa g_n) C02^T,
+    kappa = kappa^(b), delta^(b) X_n = sum_i beta_i X_{n-i}.
+
+    hist: [order][p][m][n] with hist[i] = X_{n-i}; only the first nvalid
+    (default: order) are known.  A step with v known states uses BDF min(order,
+    v).  g: one array or [nsteps][p][m][n] (g[s] drives step s).  bc: Dirichlet
+    data as in ``poisson`` (lifting per step with that step's operator).
+    Returns the new history (slot i = X_{n+nsteps-i}; slots beyond the known
+    states are zero), plus the list of all new states when return_all."""
+    hist = np.array(hist, dtype=np.float64, copy=True)
+    order = int(order)
+    _, p, m, n = hist.shape
+    v = order if nvalid is None else int(nvalid)
+    known = [hist[i] for i in range(v)]                # newest first
+    g = np.asarray(g, dtype=np.float64)
+    W = lifting(bc) if bc is not None else None
+    todo = range(p) if slices is None else slices
+    systems = {}
+    new = []
+    for step in range(nsteps):
+        b = min(order, len(known))
+        kap, beta = bdf_coefficients(b)
+        kappa = float(kap) * dt
+        if b not in systems:
+            systems[b] = _systems(m, n, p, 'heat', kappa * alpha)
+        sys_ = systems[b]
+        gn = g[step] if g.ndim == 4 else g
+        delta = sum(float(beta[i]) * known[i] for i in range(b))
+        Xn = np.zeros((p, m, n))
+        for s in todo:
+            k = slice_wavenumber(s, p)
+            ms, bs = sys_[k]
+            if W is not None and brute:
+                Xn[s] = bordered_solve(m, n, k, 'heat', kappa * alpha, delta[s] + kappa * gn[s], W[s])
+                continue
+            E = ms.rhs(delta[s] + kappa * gn[s])
+            if W is not None:
+                E = E - ms.full_apply(W[s])
+            Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+            Xn[s] = ms.expand(Y) + (W[s] if W is not None else 0.0)
+        known = [Xn] + known[:order - 1]
+        new.append(Xn)
+    out = np.zeros_like(hist)
+    for i, X in enumerate(known):
+        out[i] = X
+    return (out, new) if return_all else out
 
 
 def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None, bc=None):
