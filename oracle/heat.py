@@ -193,6 +193,65 @@ def heat_bdf(hist, g, alpha, dt, order, nsteps, nvalid=None, slices=None, brute=
     return (out, new) if return_all else out
 
 
+def heat_bdf_adjoint(hist, g, alpha, dt, order, nsteps, dL_dhistN, nvalid=None, slices=None, bc=None):
+    """Reverse-mode derivatives of L(final history) for ``heat_bdf``.
+
+    Returns (dL/dhist0, dL/dg, dL/dalpha): dL/dhist0 is [order][p][m][n] with
+    slot i = dL/dX_{-i} (zero beyond the known states), dL/dg has the shape of
+    g.  Step s (order b, kappa = kappa^(b) h): E = Rhs(sum_i beta_i X_{s-i} +
+    kappa g_s), Y = Sylv^-1 E, X_{s+1} = S Y S^T (+ W).  Reverse: lam_j =
+    dL/dX_j accumulated; mu = S^T lam_{s+1} S; Lam = Sylv^-T mu; w = Rhs^T Lam;
+    lam_{s-i} += beta_i w; dL/dg_s = kappa w; dL/dalpha -= <Lam, dSylv/dalpha Y>
+    (+ the derivative of the lifted right side, as in ``heat_adjoint``)."""
+    hist = np.asarray(hist, dtype=np.float64)
+    order = int(order)
+    _, p, m, n = hist.shape
+    v0 = order if nvalid is None else int(nvalid)
+    g = np.asarray(g, dtype=np.float64)
+    const_g = g.ndim == 3
+    W = lifting(bc) if bc is not None else np.zeros((p, m, n))
+    _, new = heat_bdf(hist, g, alpha, dt, order, nsteps, nvalid=v0, slices=slices, bc=bc, return_all=True)
+    # states by time index j = -(v0-1) .. nsteps
+    X = {-i: hist[i] for i in range(v0)}
+    for s, Xs in enumerate(new):
+        X[s + 1] = Xs
+    lam = {j: np.zeros((p, m, n)) for j in X}
+    for i in range(min(order, v0 + nsteps)):
+        lam[nsteps - i] = lam[nsteps - i] + dL_dhistN[i]
+    todo = range(p) if slices is None else slices
+    dg = np.zeros_like(g)
+    dalpha = 0.0
+    systems = {}
+    for s in reversed(range(nsteps)):
+        b = min(order, v0 + s)
+        kap, beta = bdf_coefficients(b)
+        kappa = float(kap) * dt
+        if b not in systems:
+            systems[b] = _systems(m, n, p, 'heat', kappa * alpha)
+        sys_ = systems[b]
+        for sl in todo:
+            ms, bs = sys_[slice_wavenumber(sl, p)]
+            mu = ms.expand_T(lam[s + 1][sl])
+            Lam = bs.solve_T(mu)
+            w = ms.rhs_T(Lam)
+            for i in range(b):
+                lam[s - i][sl] += float(beta[i]) * w
+            if const_g:
+                dg[sl] += kappa * w
+            else:
+                dg[s, sl] = kappa * w
+            Y = np.linalg.lstsq(ms.Sr, np.linalg.lstsq(ms.Sz, (X[s + 1][sl] - W[sl]).T, rcond=None)[0].T,
+                                rcond=None)[0]
+            dS = kappa * (ms.dA @ Y @ ms.B.T + ms.C @ Y @ ms.dD.T)
+            if bc is not None:
+                dS = dS + kappa * ms.full_apply_dka(W[sl])
+            dalpha -= float(np.sum(Lam * dS))
+    out = np.zeros_like(hist)
+    for i in range(v0):
+        out[i] = lam[-i]
+    return out, dg, dalpha
+
+
 def heat_adjoint(X0, g, alpha, dt, nsteps, dL_dXN, slices=None, bc=None):
     """Reverse-mode derivatives of L(X_N) for the BDF1 stepping above.
 

@@ -114,3 +114,69 @@ def test_lifting_in_bdf_run():
     U = tr.vals2coeffs(uv)
     out = heat.heat_bdf(np.stack([U] * 3), G, 0.5, 0.1, 3, 4, bc=uv)
     assert np.abs(out - U[None]).max() < 1e-12 * np.abs(U).max()
+
+
+def _bdf_problem(order, nvalid, steps, seed, p=4, m=7, n=6, varying=True):
+    rng = np.random.default_rng(seed)
+    hist = np.zeros((order, p, m, n))
+    for i in range(nvalid):
+        hist[i] = inputs.smooth_coeffs(p, m, n, 1.3, rng)
+    g = (np.stack([inputs.smooth_coeffs(p, m, n, 1.3, rng) for _ in range(steps)]) if varying
+         else inputs.smooth_coeffs(p, m, n, 1.3, rng))
+    tgt = np.stack([inputs.smooth_coeffs(p, m, n, 1.3, rng) for _ in range(order)])
+    return hist, g, tgt
+
+
+@pytest.mark.parametrize('order,nvalid,steps,varying,wall', [(2, 1, 4, True, False), (4, 1, 6, False, False),
+                                                             (4, 3, 3, True, True), (3, 3, 2, True, False),
+                                                             (4, 4, 2, False, False)])
+def test_bdf_adjoint_matches_central_differences(order, nvalid, steps, varying, wall):
+    """L = sum over the final history of |X - target|^2 (only the known
+    slots): gradients w.r.t. the initial history, g and alpha against central
+    differences of the forward run."""
+    alpha, dt = 0.6, 0.02
+    hist, g, tgt = _bdf_problem(order, nvalid, steps, 40 + order + nvalid, varying=varying)
+    bc = tr.coeffs2vals(inputs.smooth_coeffs(4, 7, 6, 1.1, np.random.default_rng(1))) if wall else None
+    keep = min(order, nvalid + steps)
+
+    def loss(h_, g_, a_):
+        out = heat.heat_bdf(h_, g_, a_, dt, order, steps, nvalid=nvalid, bc=bc)
+        return float(np.sum((out[:keep] - tgt[:keep]) ** 2))
+
+    out = heat.heat_bdf(hist, g, alpha, dt, order, steps, nvalid=nvalid, bc=bc)
+    dout = np.zeros_like(out)
+    dout[:keep] = 2.0 * (out[:keep] - tgt[:keep])
+    dh, dg, dal = heat.heat_bdf_adjoint(hist, g, alpha, dt, order, steps, dout, nvalid=nvalid, bc=bc)
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    d = np.zeros_like(hist)
+    d[:nvalid] = rng.standard_normal(hist[:nvalid].shape)
+    fd = (loss(hist + h * d, g, alpha) - loss(hist - h * d, g, alpha)) / (2 * h)
+    assert abs(fd - float(np.sum(dh * d))) <= 1e-7 * abs(fd)
+    assert np.all(dh[nvalid:] == 0.0)
+    d = rng.standard_normal(g.shape)
+    fd = (loss(hist, g + h * d, alpha) - loss(hist, g - h * d, alpha)) / (2 * h)
+    assert abs(fd - float(np.sum(dg * d))) <= 1e-7 * abs(fd)
+    ha = 1e-4 * alpha
+    fd = (loss(hist, g, alpha + ha) - loss(hist, g, alpha - ha)) / (2 * ha)
+    assert abs(fd - dal) <= 1e-7 * abs(fd)
+
+
+def test_bdf_adjoint_is_dense_transpose():
+    """Assemble the linear map (initial history) -> (final history) of a BDF 3
+    run with start-up column by column; the adjoint applied to c equals
+    Phi^T c."""
+    order, nvalid, steps = 3, 2, 4
+    hist, g, _ = _bdf_problem(order, nvalid, steps, 9, p=2, m=6, n=5)
+    zero_g = np.zeros_like(g)
+    shape = hist[:nvalid].shape
+    size_in = int(np.prod(shape))
+    cols = []
+    for col in range(size_in):
+        e = np.zeros(size_in); e[col] = 1.0
+        h0 = np.zeros_like(hist); h0[:nvalid] = e.reshape(shape)
+        cols.append(heat.heat_bdf(h0, zero_g, 0.5, 0.03, order, steps, nvalid=nvalid).ravel())
+    Phi = np.array(cols).T
+    c = np.random.default_rng(3).standard_normal(hist.shape)
+    dh, _, _ = heat.heat_bdf_adjoint(hist, zero_g, 0.5, 0.03, order, steps, c, nvalid=nvalid)
+    assert np.allclose(dh[:nvalid].ravel(), Phi.T @ c.ravel(), atol=1e-12 * np.abs(Phi).max())
