@@ -99,6 +99,18 @@ typedef enum {
 cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alpha,
                     double dt, double adi_tol, unsigned flags, void *stream);
 
+/*
+ * cyl_plan_bdf -- cyl_plan for runs of the b-th order BDF, b = bdf_order in
+ * 1..4 (Section 3: BDF 1, BDF 4, and the kappa^(b), delta^(b) definitions;
+ * orders 2 and 3 from the same backward-difference family:
+ * kappa^(b)/h = 1, 2/3, 6/11, 12/25).  With CYL_WITH_HEAT the plan holds the
+ * factors of every order 1..b (the first steps of a run use lower orders, see
+ * cyl_heat_step_bdf), so it needs about b times the factor memory of
+ * cyl_plan.  cyl_plan(...) is cyl_plan_bdf(..., 1, ...).
+ */
+cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alpha,
+                        double dt, double adi_tol, int bdf_order, unsigned flags, void *stream);
+
 /* Release a plan and all memory it owns (NULL is accepted). */
 cyl_status cyl_destroy(cyl_plan_t plan);
 
@@ -160,6 +172,58 @@ cyl_status cyl_heat_step(cyl_plan_t plan, double *T, const double *g, long long 
  * T_{n+1} = u0 + W with u0 of zero data.  T_0 itself need not meet the data. */
 cyl_status cyl_heat_step_bc(cyl_plan_t plan, double *T, const double *g, long long g_step_stride,
                             int nsteps, const double *bc, double *ckpt, int ckpt_every);
+
+/*
+ * cyl_heat_step_bdf -- nsteps steps of the b-th order BDF (b = the plan's
+ * bdf_order): eq. HelmholtzMatEqn with kappa = kappa^(b) and right side
+ * R_2 (delta^(b) X_n + kappa g_n) C02^T, delta^(b) X_n = sum_i beta_i X_{n-i}.
+ *
+ *   hist     device, b * N float64 coefficients; slot i (hist + i * N) holds
+ *            X_{n-i}, i = 0 the newest.  In/out: on return slot i holds
+ *            X_{n+nsteps-i}.
+ *   nvalid   1..b: how many slots hold known states on entry.  While fewer
+ *            than b states are known a step uses BDF v (v = states known),
+ *            one launch per such start-up step; slots beyond
+ *            min(b, nvalid + nsteps) are unspecified on return.
+ *   g, g_step_stride, bc   as for cyl_heat_step_bc (g + s * stride drives
+ *            step s; bc: time-constant Dirichlet data or NULL).
+ * The history is a ring inside the kernels (each step overwrites the oldest
+ * slot); one elementwise pass at the end restores the slot order above.
+ * Needs a plan from cyl_plan_bdf with CYL_WITH_HEAT.
+ */
+cyl_status cyl_heat_step_bdf(cyl_plan_t plan, double *hist, int nvalid, const double *g,
+                             long long g_step_stride, int nsteps, const double *bc);
+
+/*
+ * cyl_heat_adjoint_bdf -- reverse-mode derivatives of a scalar loss of the
+ * final history of the run cyl_heat_step_bdf(hist0, nvalid, g, g_step_stride,
+ * nsteps, bc) computes (not in the paper: the transpose of that multistep
+ * map).  Backward through the steps, with lam_j = dL/dX_j accumulated:
+ * w = (step map of BDF b)^T lam_{s+1}; lam_{s-i} += beta_i w; dL/dg_s =
+ * kappa^(b) w; dL/dalpha += <w, X_{s+1} - delta^(b) X_s - kappa^(b) g_s> / alpha
+ * (the BDF b analogue of the identity of cyl_heat_adjoint, on the lifted
+ * states when bc != NULL).  Start-up steps use their own order, as forward.
+ *
+ *   hist0, nvalid, g, g_step_stride, nsteps, bc   as for cyl_heat_step_bdf
+ *               (hist0 is not modified; may be NULL when dL_dalpha is NULL).
+ *   dL_dhistN   device, b * N float64: dL/d(final history), slot i = dL/dX_{N-i}
+ *               (slots beyond min(b, nvalid + nsteps) are ignored).
+ *   dL_dhist0   device, b * N float64 output, slot i = dL/dX_{-i} for
+ *               i < nvalid, zero beyond (may alias dL_dhistN).
+ *   dL_dg, dL_dalpha, ckpt_every   as for cyl_heat_adjoint (checkpoints hold
+ *               whole histories: b states every ckpt_every steps).
+ *   workspace   device memory of at least cyl_heat_adjoint_bdf_workspace()
+ *               bytes (always needed: the adjoint ring of b + 1 states).
+ * Needs a plan from cyl_plan_bdf with CYL_WITH_HEAT.
+ */
+cyl_status cyl_heat_adjoint_bdf(cyl_plan_t plan, const double *hist0, int nvalid, const double *g,
+                                long long g_step_stride, int nsteps, const double *bc, int ckpt_every,
+                                const double *dL_dhistN, double *dL_dhist0, double *dL_dg,
+                                double *dL_dalpha, void *workspace, size_t workspace_bytes);
+
+/* Bytes of device workspace cyl_heat_adjoint_bdf needs. */
+cyl_status cyl_heat_adjoint_bdf_workspace(cyl_plan_t plan, int nsteps, int ckpt_every, int need_alpha,
+                                          size_t *bytes);
 
 /*
  * cyl_heat_adjoint -- reverse-mode derivatives of a scalar loss L(T_N) of the
@@ -300,7 +364,8 @@ const char *cyl_status_string(cyl_status s);
  * Host-side introspection (no device access; valid on CYL_HOST_ONLY plans).
  * ------------------------------------------------------------------------- */
 
-/* which: 0 = Poisson, 1 = heat.  k = |wavenumber| in 0 .. n_theta/2;
+/* which: 0 = Poisson, b = 1..4 = the BDF b step (1 = the BDF1 heat step;
+ * 2..4 only on plans from cyl_plan_bdf).  k = |wavenumber| in 0 .. n_theta/2;
  * parity = radial parity block (0 or 1).
  * Returns J and, when the pointers are non-NULL, the spectral interval
  * [a, b] of the radial pencil, [c, d] of the vertical pencil (Section 3, the
@@ -325,7 +390,7 @@ cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int pari
 cyl_status cyl_grid(cyl_plan_t plan, double *r, double *z, double *theta);
 
 /* Algorithmic FP64 flops of nsteps steps of the fused ADI kernel (which: 0
- * Poisson, 1 heat; transposed: 0 forward, 1 adjoint), counting 2 per fused
+ * Poisson, b heat BDF b; transposed: 0 forward, 1 adjoint), counting 2 per fused
  * multiply-add: the right side (3 + 5 per element), Algorithm 1 (radial
  * sweep 12 and vertical sweep 8 per element and iteration, minus the radial
  * apply of the first and the vertical apply of the last iteration) and the

@@ -22,11 +22,12 @@ struct cyl_plan_s {
   bool host_only = false;
   int device = 0;
   double *d_fac = nullptr;
-  Item *d_items[2] = {nullptr, nullptr};
-  int nitems[2] = {0, 0};
-  int threads[2] = {0, 0};
-  size_t smem[2] = {0, 0};
-  int use_smem[2] = {1, 1};
+  // per kind: 0 = Poisson, b = 1..4 = BDF b step
+  Item *d_items[cyl::kNumKinds] = {};
+  int nitems[cyl::kNumKinds] = {};
+  int threads[cyl::kNumKinds] = {};
+  size_t smem[cyl::kNumKinds] = {};
+  int use_smem[cyl::kNumKinds] = {1, 1, 1, 1, 1};
   int ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
   long long gwork_per_item = 0;
   double *d_gwork = nullptr;
@@ -158,18 +159,16 @@ cyl_status prepare_lift(cyl_plan_s *P, int kind, const double *bc) {
     return from_cuda(e);
   }
   cyl::AdiArgs a = adi_args(P, kind);
-  const double c0 = kind == 1 ? 1.0 : 0.0;
-  const double c1 = kind == 1 ? P->hp.alpha * P->hp.dt : 1.0;
+  // step operator of BDF b (kind b >= 1): c0 = 1, c1 = kappa^(b) alpha; Poisson: c0 = 0, c1 = 1
+  const double c0 = kind >= 1 ? 1.0 : 0.0;
+  const double c1 = kind >= 1 ? P->hp.alpha * P->hp.dt * cyl::bdf_kappa(kind) : 1.0;
   return from_cuda(cyl::launch_lift(a, bc, P->d_corr, P->d_lift, P->d_corr, c0, c1, P->d_W[4], P->d_W[0],
                                     P->d_W[2], P->d_tmp[0], P->d_tmp[1], std::min(P->threads[kind], 256), P->st));
 }
 
-cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
-                   long long gstride, int nsteps, double *ckpt, int ckpt_every, bool lifted = false) {
-  cyl::AdiArgs a{};
-  a.items = P->d_items[kind];
-  a.nitems = P->nitems[kind];
-  a.fac = P->d_fac;
+cyl::AdiArgs step_args(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
+                       long long gstride, int nsteps, double *ckpt, int ckpt_every, bool lifted) {
+  cyl::AdiArgs a = adi_args(P, kind);
   a.Xin = Xin;
   a.Xout = Xout;
   a.G = G;
@@ -178,23 +177,14 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   a.nsteps = nsteps;
   a.ckpt = ckpt;
   a.ckpt_every = ckpt_every > 0 ? ckpt_every : 1;
-  a.m = P->hp.m;
-  a.n = P->hp.n;
-  a.p = P->hp.p;
-  a.zero_other = (P->hp.flags & CYL_BOTH_PARITIES) ? 0 : 1;
-  a.transpose = 0;
-  a.gwork = P->d_gwork;
-  a.gwork_per_item = P->gwork_per_item;
-  a.use_smem = P->use_smem[kind];
-  a.ld = P->ld;
-  a.smem_rows = P->smem_rows;
-  a.maxM = P->maxM;
-  a.maxNz = P->maxNz;
-  a.err = P->d_err;
-  a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
-  a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
   a.lift = lifted ? P->d_lift : nullptr;
   a.corr = lifted ? P->d_corr : nullptr;
+  return a;
+}
+
+cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
+                   long long gstride, int nsteps, double *ckpt, int ckpt_every, bool lifted = false) {
+  cyl::AdiArgs a = step_args(P, kind, Xin, Xout, G, kappa, gstride, nsteps, ckpt, ckpt_every, lifted);
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
@@ -337,6 +327,11 @@ double cyl_jacobi_dn(double u, double kprime) { return cyl::jacobi_dn(u, kprime)
 
 cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alpha, double dt, double adi_tol,
                     unsigned flags, void *stream) {
+  return cyl_plan_bdf(plan, n_r, n_z, n_theta, alpha, dt, adi_tol, 1, flags, stream);
+}
+
+cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alpha, double dt,
+                        double adi_tol, int bdf_order, unsigned flags, void *stream) {
   if (!plan) return CYL_EINVAL;
   *plan = nullptr;
   if (n_r < 4 || n_z < 4 || n_theta < 2 || (n_theta & 1)) return CYL_EINVAL;
@@ -346,11 +341,12 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
                           CYL_TEST_NO_TMA | CYL_WITH_BC))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
+  if (bdf_order < 1 || bdf_order > cyl::kMaxBdf) return CYL_EINVAL;
   if ((long long)n_r * n_z * n_theta > (1LL << 40)) return CYL_EINVAL;
   cyl_plan_s *P = new (std::nothrow) cyl_plan_s();
   if (!P) return CYL_ENOMEM;
   try {
-    std::string err = cyl::build_host_plan(P->hp, n_r, n_z, n_theta, alpha, dt, adi_tol, flags);
+    std::string err = cyl::build_host_plan(P->hp, n_r, n_z, n_theta, alpha, dt, adi_tol, flags, bdf_order);
     if (!err.empty()) {
       delete P;
       return CYL_EINVAL;
@@ -371,10 +367,10 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   P->maxNz = std::max(h.Nc[0], h.Nc[1]);
   P->smem_rows = std::max(h.Mfull[0], h.Mfull[1]);
   int maxW = 0;
-  for (int kind = 0; kind < 2; ++kind)
+  for (int kind = 0; kind < cyl::kNumKinds; ++kind)
     for (const Item &it : h.kind[kind].items) maxW = std::max(maxW, it.nsl * it.Nzfull);
   P->ld = std::max(1, maxW) | 1;
-  for (int kind = 0; kind < 2; ++kind) {
+  for (int kind = 0; kind < cyl::kNumKinds; ++kind) {
     int thr = 32;
     for (const Item &it : h.kind[kind].items) thr = std::max(thr, std::max(it.nsl * it.Nz, it.nsl * it.M));
     P->threads[kind] = (thr + 31) / 32 * 32;
@@ -386,17 +382,18 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
     P->use_smem[kind] = level;
     P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, level);
   }
-  if (P->threads[0] > 512 || P->threads[1] > 512) {
-    delete P;
-    return CYL_EINVAL;
-  }
+  for (int kind = 0; kind < cyl::kNumKinds; ++kind)
+    if (P->threads[kind] > 512) {
+      delete P;
+      return CYL_EINVAL;
+    }
   if (P->host_only) {
     *plan = P;
     return CYL_OK;
   }
   cudaError_t e = cudaGetDevice(&P->device);
   if (e == cudaSuccess) e = upload(&P->d_fac, h.factors.data(), h.factors.size());
-  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+  for (int kind = 0; kind < cyl::kNumKinds && e == cudaSuccess; ++kind) {
     P->nitems[kind] = (int)h.kind[kind].items.size();
     e = upload(&P->d_items[kind], h.kind[kind].items.data(), h.kind[kind].items.size());
   }
@@ -408,9 +405,11 @@ cyl_status cyl_plan(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double alph
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_apart, std::max(1, P->nitems[1]) * sizeof(double));
   if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_lift, P->N * sizeof(double));
   if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_corr, P->N * sizeof(double));
-  if (e == cudaSuccess && !(P->use_smem[0] == 2 && P->use_smem[1] == 2)) {
+  bool all_smem = true;
+  for (int kind = 0; kind < cyl::kNumKinds; ++kind) all_smem = all_smem && P->use_smem[kind] == 2;
+  if (e == cudaSuccess && !all_smem) {
     P->gwork_per_item = ((long long)P->smem_rows * P->ld + (long long)P->maxM * P->ld + 31) / 32 * 32;
-    const int maxItems = std::max(P->nitems[0], P->nitems[1]);
+    const int maxItems = *std::max_element(P->nitems, P->nitems + cyl::kNumKinds);
     e = cudaMalloc((void **)&P->d_gwork, (size_t)P->gwork_per_item * maxItems * sizeof(double));
   }
   if (e != cudaSuccess) {
@@ -479,6 +478,189 @@ cyl_status cyl_heat_step_bc(cyl_plan_t P, double *T, const double *g, long long 
     if (s != CYL_OK) return s;
   }
   return run_adi(P, 1, T, T, g, P->hp.dt, g ? g_step_stride : 0, nsteps, ckpt, ckpt_every, bc != nullptr);
+}
+
+// nsteps BDF steps on a history ring of ring_len slots (slot (base + i) % ring_len
+// holds X_{n-i}; v states known).  Start-up steps (v < order) run one launch
+// each at order v; the rest run in one launch.  g + (s0 + s) * gstride drives
+// step s.  Updates base and v; lifted_kind tracks which order's lifting
+// correction the plan's lifting arrays hold.
+cyl_status bdf_forward(cyl_plan_s *P, double *ring, int ring_len, int &base, int &v, int s0, int nsteps,
+                       const double *g, long long gstride, const double *bc, int &lifted_kind) {
+  const int order = P->hp.bdf_order;
+  for (int s = 0; s < nsteps;) {
+    const int b = std::min(order, v);                  // start-up through lower orders
+    const int cnt = b < order ? 1 : nsteps - s;
+    if (bc && lifted_kind != b) {
+      cyl_status st = prepare_lift(P, b, bc);
+      if (st != CYL_OK) return st;
+      lifted_kind = b;
+    }
+    const double *Gs = g ? g + (size_t)(s0 + s) * (size_t)gstride : nullptr;
+    cyl::AdiArgs a = step_args(P, b, nullptr, nullptr, Gs, P->hp.dt * cyl::bdf_kappa(b), g ? gstride : 0, cnt,
+                               nullptr, 1, bc != nullptr);
+    a.hist = ring;
+    a.hist_stride = (long long)P->N;
+    a.hist_b = ring_len;
+    a.hist_base = base;
+    a.order = b;
+    cyl::bdf_beta(b, a.beta);
+    cudaError_t e = cyl::launch_adi(a, P->threads[b], P->smem[b], P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    base = ((base - cnt) % ring_len + ring_len) % ring_len;
+    v = std::min(order, v + cnt);
+    s += cnt;
+  }
+  return CYL_OK;
+}
+
+// dst slot i = src slot (base + i) % b, i < b (canonical order of a ring).
+cudaError_t copy_canonical(double *dst, const double *src, size_t N, int b, int base, cudaStream_t st) {
+  cyl::SlotMap map{};
+  for (int i = 0; i < b; ++i) map.src[i] = (base + i) % b;
+  return cyl::launch_permute_slots(dst, src, (long long)N, b, map, st);
+}
+
+cyl_status cyl_heat_step_bdf(cyl_plan_t P, double *hist, int nvalid, const double *g, long long g_step_stride,
+                             int nsteps, const double *bc) {
+  if (!P || !hist || nsteps < 0 || g_step_stride < 0) return CYL_EINVAL;
+  if (P->is_batch || P->host_only) return CYL_ESTATE;
+  const int order = P->hp.bdf_order;
+  if (nvalid < 1 || nvalid > order) return CYL_EINVAL;
+  if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
+  for (int b = 1; b <= order; ++b)
+    if (!P->hp.kind[b].built) return CYL_ESTATE;
+  int base = 0, v = nvalid, lifted_kind = -1;
+  cyl_status s = bdf_forward(P, hist, order, base, v, 0, nsteps, g, g_step_stride, bc, lifted_kind);
+  if (s != CYL_OK) return s;
+  if (base != 0) return from_cuda(copy_canonical(hist, hist, P->N, order, base, P->st));
+  return CYL_OK;
+}
+
+static size_t bdf_adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, bool need_alpha) {
+  const size_t order = P->hp.bdf_order;
+  size_t d = (order + 1) * P->N;                        // adjoint ring lam_j
+  if (need_alpha && nsteps > 0) {
+    const long long c = std::min(ckpt_every, nsteps);
+    const long long nseg = (nsteps + c - 1) / c;
+    d += (size_t)nseg * order * P->N;                   // history checkpoints
+    d += (size_t)(c + order) * P->N;                    // one recomputed segment (reverse time order)
+  }
+  return d;
+}
+
+cyl_status cyl_heat_adjoint_bdf_workspace(cyl_plan_t P, int nsteps, int ckpt_every, int need_alpha,
+                                          size_t *bytes) {
+  if (!P || !bytes || nsteps < 0 || ckpt_every < 1) return CYL_EINVAL;
+  *bytes = bdf_adjoint_workspace_doubles(P, nsteps, ckpt_every, need_alpha != 0) * sizeof(double);
+  return CYL_OK;
+}
+
+cyl_status cyl_heat_adjoint_bdf(cyl_plan_t P, const double *hist0, int nvalid, const double *g,
+                                long long g_step_stride, int nsteps, const double *bc, int ckpt_every,
+                                const double *dL_dhistN, double *dL_dhist0, double *dL_dg, double *dL_dalpha,
+                                void *workspace, size_t workspace_bytes) {
+  if (!P || !dL_dhistN || !dL_dhist0 || nsteps < 0 || ckpt_every < 1 || g_step_stride < 0) return CYL_EINVAL;
+  if (P->is_batch || P->host_only) return CYL_ESTATE;
+  const int order = P->hp.bdf_order, R = order + 1, jofs = order;
+  if (nvalid < 1 || nvalid > order) return CYL_EINVAL;
+  if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
+  if (dL_dalpha && !hist0) return CYL_EINVAL;
+  for (int b = 1; b <= order; ++b)
+    if (!P->hp.kind[b].built) return CYL_ESTATE;
+  const size_t need = bdf_adjoint_workspace_doubles(P, nsteps, ckpt_every, dL_dalpha != nullptr);
+  if (!workspace || workspace_bytes < need * sizeof(double)) return CYL_EINVAL;
+  const size_t N = P->N;
+  double *ring = static_cast<double *>(workspace);
+  cudaError_t e = cudaSuccess;
+  // lam_{nsteps - i} = dL/dhist_N slot i for the known final slots; every other ring slot zero
+  {
+    cyl::SlotMap map{};
+    for (int k = 0; k < R; ++k) map.src[k] = -1;
+    const int keep = std::min(order, nvalid + nsteps);
+    for (int i = 0; i < keep; ++i) map.src[(nsteps - i + jofs) % R] = i;
+    e = cyl::launch_permute_slots(ring, dL_dhistN, (long long)N, R, map, P->st);
+  }
+  if (e == cudaSuccess && dL_dg && g_step_stride == 0) e = cudaMemsetAsync(dL_dg, 0, N * sizeof(double), P->st);
+  if (e == cudaSuccess && dL_dalpha)
+    e = cudaMemsetAsync(P->d_apart, 0, std::max(1, P->nitems[1]) * sizeof(double), P->st);
+  if (e != cudaSuccess) return from_cuda(e);
+  // reverse steps [lo, hi): launches of one order each (start-up steps alone)
+  auto reverse = [&](int lo, int hi, const double *traj, long long trajK) -> cyl_status {
+    for (int s_hi = hi; s_hi > lo;) {
+      const int s_top = s_hi - 1;
+      const int b = std::min(order, nvalid + s_top);
+      const int s_lo = b < order ? s_top : std::max(lo, order - nvalid);
+      cyl::AdjointArgs adj{};
+      adj.lam_ring = ring;
+      adj.R = R;
+      adj.jofs = jofs;
+      adj.order = b;
+      cyl::bdf_beta(b, adj.beta);
+      adj.G = g;
+      adj.gstride = g ? g_step_stride : 0;
+      adj.dg = dL_dg;
+      adj.dg_stride = g_step_stride;
+      adj.kappa = P->hp.dt * cyl::bdf_kappa(b);
+      adj.traj = traj;
+      adj.traj_K = trajK;
+      adj.alpha_part = traj ? P->d_apart : nullptr;
+      adj.n_lo = s_lo;
+      adj.n_hi = s_hi;
+      cyl::AdiArgs a = adi_args(P, b);
+      cudaError_t err = cyl::launch_adjoint(a, adj, P->threads[b], P->smem[b], P->st);
+      if (err != cudaSuccess) return from_cuda(err);
+      s_hi = s_lo;
+    }
+    return CYL_OK;
+  };
+  cyl_status s = CYL_OK;
+  if (!dL_dalpha) {
+    s = reverse(0, nsteps, nullptr, 0);
+  } else if (nsteps > 0) {
+    const int c = std::min(ckpt_every, nsteps);
+    const int nseg = (nsteps + c - 1) / c;
+    double *ck = ring + (size_t)R * N;                  // nseg histories, canonical order
+    double *traj = ck + (size_t)nseg * order * N;       // c + order states
+    int lifted_kind = -1;
+    e = cudaMemcpyAsync(ck, hist0, (size_t)order * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (nseg > 1) {                                     // histories at c, 2c, ... (traj's first slots as the ring)
+      e = cudaMemcpyAsync(traj, hist0, (size_t)order * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+      if (e != cudaSuccess) return from_cuda(e);
+      int base = 0, v = nvalid;
+      for (int k = 1; k < nseg; ++k) {
+        s = bdf_forward(P, traj, order, base, v, (k - 1) * c, c, g, g_step_stride, bc, lifted_kind);
+        if (s != CYL_OK) return s;
+        e = copy_canonical(ck + (size_t)k * order * N, traj, N, order, base, P->st);
+        if (e != cudaSuccess) return from_cuda(e);
+      }
+    }
+    for (int k = nseg - 1; k >= 0; --k) {
+      const int n_lo = k * c, n_hi = std::min(n_lo + c, nsteps), len = n_hi - n_lo;
+      // X_j at traj + (n_hi - j) N: the checkpoint history fills slots len .. len + order - 1
+      e = cudaMemcpyAsync(traj + (size_t)len * N, ck + (size_t)k * order * N, (size_t)order * N * sizeof(double),
+                          cudaMemcpyDeviceToDevice, P->st);
+      if (e != cudaSuccess) return from_cuda(e);
+      int base = len, v = std::min(order, nvalid + n_lo);
+      s = bdf_forward(P, traj, len + order, base, v, n_lo, len, g, g_step_stride, bc, lifted_kind);
+      if (s != CYL_OK) return s;
+      s = reverse(n_lo, n_hi, traj, n_hi);
+      if (s != CYL_OK) return s;
+    }
+  }
+  if (s != CYL_OK) return s;
+  // dL/dhist_0 slot i = lam_{-i} for the known initial states, zero beyond
+  {
+    cyl::SlotMap map{};
+    for (int i = 0; i < cyl::kMaxSlots; ++i) map.src[i] = -1;
+    for (int i = 0; i < nvalid; ++i) map.src[i] = (-i + jofs) % R;
+    e = cyl::launch_permute_slots(dL_dhist0, ring, (long long)N, order, map, P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  if (dL_dalpha)
+    return from_cuda(cyl::launch_sum_partials(P->d_apart, P->nitems[1], 1.0 / P->hp.alpha, dL_dalpha, P->st));
+  return CYL_OK;
 }
 
 static size_t adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, bool need_alpha) {
@@ -585,7 +767,7 @@ cyl_status cyl_sync(cyl_plan_t P) {
 }
 
 cyl_status cyl_plan_flops(cyl_plan_t P, int which, int nsteps, int transposed, double *flops) {
-  if (!P || !flops || which < 0 || which > 1 || nsteps < 0) return CYL_EINVAL;
+  if (!P || !flops || which < 0 || which >= cyl::kNumKinds || nsteps < 0) return CYL_EINVAL;
   const std::vector<Item> &items = P->is_batch ? P->bitems : P->hp.kind[which].items;
   if (P->is_batch && which != 1) return CYL_ESTATE;
   double f = 0.0;
@@ -600,6 +782,8 @@ cyl_status cyl_plan_flops(cyl_plan_t P, int which, int nsteps, int transposed, d
       per_step = 1.5 * M * W + (12.0 * it.J - 6.0 + 8.0 * it.J - 4.0) * M * W + 3.0 * M * Wf +
                  5.0 * it.Mfull * Wf;
     }
+    // BDF b > 1: delta^(b) X_n, b - 1 further fused multiply-adds per class element
+    if (!transposed && which >= 2) per_step += (which - 1.0) * it.Mfull * it.nsl * it.Nzfull;
     f += 2.0 * per_step * nsteps;   // 2 flops per fused multiply-add
   }
   *flops = f;
@@ -622,7 +806,7 @@ cyl_status cyl_grid(cyl_plan_t P, double *r, double *z, double *theta) {
 
 cyl_status cyl_plan_shifts(cyl_plan_t P, int which, int k, int parity, int *J, double *interval4,
                            double *p_shift, double *q_shift) {
-  if (!P || !J || which < 0 || which > 1 || k < 0 || k > P->hp.p / 2 || parity < 0 || parity > 1)
+  if (!P || !J || which < 0 || which >= cyl::kNumKinds || k < 0 || k > P->hp.p / 2 || parity < 0 || parity > 1)
     return CYL_EINVAL;
   if (P->is_batch) return CYL_ESTATE;
   const auto &KT = P->hp.kind[which];
@@ -639,20 +823,20 @@ cyl_status cyl_plan_shifts(cyl_plan_t P, int which, int k, int parity, int *J, d
 }
 
 cyl_status cyl_plan_operator(cyl_plan_t P, int op, int which, int k, int parity, int *dim, double *out) {
-  if (!P || !dim || op < 0 || op > 3 || which < 0 || which > 1 || parity < 0 || parity > 1 || k < 0 ||
+  if (!P || !dim || op < 0 || op > 3 || which < 0 || which >= cyl::kNumKinds || parity < 0 || parity > 1 || k < 0 ||
       k > P->hp.p / 2)
     return CYL_EINVAL;
   if (P->is_batch) return CYL_ESTATE;
   const HostPlan &h = P->hp;
-  if (which == 1 && !(h.alpha > 0 && h.dt > 0)) return CYL_ESTATE;
-  const double ka = which == 1 ? h.alpha * h.dt : 1.0;
+  if (which >= 1 && !(h.alpha > 0 && h.dt > 0)) return CYL_ESTATE;
+  const double ka = which >= 1 ? h.alpha * h.dt * cyl::bdf_kappa(which) : 1.0;
   cyl::Band B;
   if (op == 0) {
     cyl::Band L = h.Lblk(k, parity), C = h.Cblk(parity);
     B = cyl::Band(L.n, 2, 3);
     for (int i = 0; i < L.n; ++i)
       for (int j = std::max(0, i - 2); j <= std::min(L.n - 1, i + 3); ++j)
-        B.at(i, j) = which == 1 ? C.get(i, j) - ka * L.get(i, j) : -L.get(i, j);
+        B.at(i, j) = which >= 1 ? C.get(i, j) - ka * L.get(i, j) : -L.get(i, j);
   } else if (op == 1) {
     B = h.Cblk(parity);
   } else if (op == 2) {

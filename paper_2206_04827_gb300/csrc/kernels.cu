@@ -350,26 +350,44 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
   const double *c02 = a.fac + it.c02off;
   const long long c0 = c, c_end = c0 + (long long)a.nsteps * it.J;
   if (tid == 0 && !a.test_no_tma) issue_tables<false>(sh, a, it, c0, c0);
-  const double *Xsrc = a.Xin + it.xoff;
-  double *Xout = a.Xout + it.xoff;
+  const bool ring = a.hist_b > 0;
+  const double *Xsrc = ring ? nullptr : a.Xin + it.xoff;
+  double *Xout = ring ? nullptr : a.Xout + it.xoff;
   const double *lift = a.lift ? a.lift + it.xoff : nullptr;
   const double *Gbase = a.G ? a.G + it.xoff : nullptr;
+  int base = a.hist_base;
   for (int step = 0; step < a.nsteps; ++step) {
     const double *Gs = Gbase ? Gbase + (size_t)step * a.gstride : nullptr;
-    // Right side of eq. HelmholtzMatEqn, E = trunc(R_2 (X + kappa g) C02^T), in two
-    // banded passes: T1 = (X + kappa g) C02^T on the class rows, then E = R_2 T1.
+    const double *hs[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (ring) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < a.order) hs[i] = a.hist + (size_t)((base + i) % a.hist_b) * a.hist_stride + it.xoff;
+      Xout = a.hist + (size_t)((base + a.hist_b - 1) % a.hist_b) * a.hist_stride + it.xoff;
+    }
+    // Right side of eq. HelmholtzMatEqn, E = trunc(R_2 (delta X + kappa g) C02^T), in two
+    // banded passes: T1 = (delta X + kappa g) C02^T on the class rows, then E = R_2 T1
+    // (delta X = X_n for BDF1, sum_i beta_i X_{n-i} from the history ring otherwise).
     for (int e = tid; e < it.Mfull * W; e += nth) {
       const int ap = e / W, cc = e - ap * W;
       const int sl = cc / Nz, b = cc - sl * Nz;
       const int i = it.pr + 2 * ap, j = it.pz + 2 * b;
-      const size_t base = (size_t)(it.s0 + sl) * slice + (size_t)i * n;
+      const size_t row = (size_t)(it.s0 + sl) * slice + (size_t)i * n;
       double acc = 0.0;
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
         const int jj = j + 2 * t;
         if (jj < n) {
-          double z = Xsrc[base + jj];
-          if (Gs) z = fma(a.kappa, Gs[base + jj], z);
+          double z;
+          if (ring) {
+            z = 0.0;
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+              if (h < a.order) z = fma(a.beta[h], hs[h][row + jj], z);
+          } else {
+            z = Xsrc[row + jj];
+          }
+          if (Gs) z = fma(a.kappa, Gs[row + jj], z);
           acc = fma(c02[b * C02STRIDE + t], z, acc);
         }
       }
@@ -427,6 +445,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     gp.sync();
     Xsrc = Xout;
+    if (ring) base = (base + a.hist_b - 1) % a.hist_b;
   }
 }
 
@@ -563,14 +582,16 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
   bool timed_out = false;
   double apart = 0.0;
   double *lam = g.lam;
+  const bool ring = g.lam_ring != nullptr;
   long long c = 0;
   for (int n_step = g.n_hi - 1; n_step >= g.n_lo; --n_step) {
+    double *lin = ring ? g.lam_ring + (size_t)((n_step + 1 + g.jofs) % g.R) * Ntot : lam;
     // mu[a][b] = lam[a][b] - lam[a][b+1] - lam[a+1][b] + lam[a+1][b+1] (class indices)
     for (int e = tid; e < M * W; e += nth) {
       const int aa = e / W, cc = e - aa * W;
       const int sl = cc / Nz, b = cc - sl * Nz;
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * aa) * n + it.pz + 2 * b;
-      Fa[aa * ld + cc] = lam[o] - lam[o + 2] - lam[o + 2 * n] + lam[o + 2 * n + 2];
+      Fa[aa * ld + cc] = lin[o] - lin[o + 2] - lin[o + 2 * n] + lin[o + 2 * n + 2];
     }
     __syncthreads();
     adi_iterations<true, SMEM ? 2 : 8>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
@@ -590,7 +611,19 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
     // lam_n = R_2^T T1 on all class rows; forcing gradient and alpha term
     const double *Gn = g.G ? g.G + (size_t)n_step * g.gstride : nullptr;
     double *dgn = g.dg ? g.dg + (size_t)n_step * g.dg_stride : nullptr;
-    const double *Xn = g.traj ? g.traj + (size_t)(n_step - g.n_lo) * Ntot : nullptr;
+    const double *Xn = (g.traj && !ring) ? g.traj + (size_t)(n_step - g.n_lo) * Ntot : nullptr;
+    double *lout[4] = {nullptr, nullptr, nullptr, nullptr};
+    const double *xr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // X_{s+1}, X_s, .., X_{s-3}
+    if (ring) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if (h < g.order) lout[h] = g.lam_ring + (size_t)((n_step - h + g.jofs) % g.R) * Ntot;
+      if (g.traj) {
+#pragma unroll
+        for (int h = 0; h < 5; ++h)
+          if (h <= g.order) xr[h] = g.traj + (size_t)(g.traj_K - (n_step + 1 - h)) * Ntot;
+      }
+    }
     for (int e = tid; e < it.Mfull * Wf; e += nth) {
       const int ap = e / Wf, cc = e - ap * Wf;
       const int sl = cc / it.Nzfull, bp = cc - sl * it.Nzfull;
@@ -601,13 +634,27 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
         if (q >= 0 && q < M) acc = fma(r2[q * R2STRIDE + s + 1], Fa[q * ld + cc], acc);
       }
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * ap) * n + it.pz + 2 * bp;
-      lam[o] = acc;
+      if (ring) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+          if (h < g.order) lout[h][o] = fma(g.beta[h], acc, lout[h][o]);
+      } else {
+        lam[o] = acc;
+      }
       if (dgn) {
         if (g.dg_stride == 0) dgn[o] += g.kappa * acc;
         else dgn[o] = g.kappa * acc;
       }
       if (Xn) {
         double d = Xn[o + Ntot] - Xn[o];
+        if (Gn) d = fma(-g.kappa, Gn[o], d);
+        apart = fma(acc, d, apart);
+      }
+      if (xr[0]) {
+        double d = xr[0][o];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+          if (h < g.order) d = fma(-g.beta[h], xr[h + 1][o], d);
         if (Gn) d = fma(-g.kappa, Gn[o], d);
         apart = fma(acc, d, apart);
       }
@@ -618,8 +665,20 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
         const int ap = e / Wf, cc = e - ap * Wf;
         const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
         const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(po + 2 * ap) * n + it.pz + 2 * b;
-        lam[o] = 0.0;
+        if (!ring) lam[o] = 0.0;
         if (dgn && g.dg_stride != 0) dgn[o] = 0.0;
+      }
+    }
+    if (ring) {
+      // lam_{s+1} is consumed: clear this item's positions of its slot (it becomes lam_{s-order})
+      const int nclass = a.zero_other ? 2 : 1;
+      for (int q = 0; q < nclass; ++q) {
+        const int pq = q == 0 ? it.pr : 1 - it.pr, Mq = (m - pq + 1) / 2;
+        for (int e = tid; e < Mq * Wf; e += nth) {
+          const int ap = e / Wf, cc = e - ap * Wf;
+          const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
+          lin[(size_t)(it.s0 + sl) * slice + (size_t)(pq + 2 * ap) * n + it.pz + 2 * b] = 0.0;
+        }
       }
     }
     __syncthreads();
@@ -720,6 +779,29 @@ cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *
   if ((e = launch_axis_matvec(tmp1, Wc_out, Wt, 1, a.p, (long long)a.m * a.n, st)) != cudaSuccess) return e;
   // corr is written (and later read) only at the items' class positions
   lift_correction_kernel<<<a.nitems, threads, 0, st>>>(a, Wc_out, corr, c0, c1);
+  return cudaGetLastError();
+}
+
+// Slot permutation of up to 5 N-element arrays: dst slot k = src slot
+// map.src[k] (a negative entry writes zeros).  Each thread owns one element
+// position of every slot and reads before it writes, so dst may equal src
+// (the history rotation of a BDF run, the adjoint's ring set-up and read-out).
+__global__ void permute_slots_kernel(double *dst, const double *src, long long N, int nd, SlotMap map) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    double v[kMaxSlots];
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < nd) v[k] = map.src[k] >= 0 ? src[(size_t)map.src[k] * N + e] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < nd) dst[(size_t)k * N + e] = v[k];
+  }
+}
+
+cudaError_t launch_permute_slots(double *dst, const double *src, long long N, int nd, const SlotMap &map,
+                                 cudaStream_t st) {
+  if (nd < 1 || nd > kMaxSlots) return cudaErrorInvalidValue;
+  permute_slots_kernel<<<(int)std::min<long long>((N + 255) / 256, 152LL * 16), 256, 0, st>>>(dst, src, N, nd, map);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,15 @@ struct AdiArgs {
   int *err;                // device status word (CYL_ERR_TIMEOUT on a bounded-wait timeout)
   long long group_doubles; // batch kernel: shared-memory slice per thread group (multiple of 32)
   long long wait_limit;    // SM clock cycles a bounded wait may spin (about 1 s normally)
+  // BDF history ring (hist_b > 0 replaces Xin / Xout): slot i at hist + i *
+  // hist_stride; at the launch's first step the newest state is in slot
+  // hist_base and X_{n-i} in slot (hist_base + i) % hist_b; each step writes
+  // the new state over the oldest slot.  The right side of every step of the
+  // launch is delta^(order) X_n + kappa g_n = sum_{i<order} beta[i] X_{n-i} + kappa g_n.
+  double *hist;
+  long long hist_stride;
+  int hist_b, hist_base, order;
+  double beta[4];
   const double *lift;      // coefficients of the lifting W of the boundary data, or NULL
   const double *corr;      // right-side correction of the lifted problem (class positions), or NULL
   int test_no_tma;         // failure-detection test: never start table copies, so waits run out
@@ -50,12 +59,27 @@ struct AdjointArgs {
   double *alpha_part;      // per-item partial sums of <lam, X_{n+1} - X_n - kappa g_n>, or NULL
   double kappa;
   int n_lo, n_hi;
+  // multistep (BDF b) mode when lam_ring != NULL (lam unused): lam_j is slot
+  // (j + jofs) % R of lam_ring (slots N apart); step s reads lam_{s+1}, adds
+  // beta[h] * w into lam_{s-h} (h < order) and clears lam_{s+1}'s slot for
+  // reuse.  traj then holds X_j at traj + (traj_K - j) * N (reverse time
+  // order) and the alpha term is <w, X_{s+1} - sum_h beta_h X_{s-h} - kappa g_s>.
+  double *lam_ring;
+  int R, jofs, order;
+  double beta[4];
+  long long traj_K;
 };
 
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
                         double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
                         int threads, cudaStream_t st);
+constexpr int kMaxSlots = 5;
+struct SlotMap {
+  int src[kMaxSlots];
+};
+cudaError_t launch_permute_slots(double *dst, const double *src, long long N, int nd, const SlotMap &map,
+                                 cudaStream_t st);
 cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st);
 
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level);

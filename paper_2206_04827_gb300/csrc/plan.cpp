@@ -364,9 +364,29 @@ static Band widen(const Band &B, int lo, int hi) {
   return W;
 }
 
+// b-th order BDF (Section 3: BDF 1, BDF 4 and the kappa^(b), delta^(b)
+// definitions), normalised so that y_{n+1} - kappa y'_{n+1} = sum_i beta_i y_{n-i}.
+// Orders 2 and 3 are the same backward-difference family as the printed
+// BDF 4: sum_{j<=b} (1/j) nabla^j y_{n+1} = h y'_{n+1}.
+double bdf_kappa(int b) {
+  static const double k[kMaxBdf + 1] = {0.0, 1.0, 2.0 / 3.0, 6.0 / 11.0, 12.0 / 25.0};
+  return (b >= 1 && b <= kMaxBdf) ? k[b] : 0.0;
+}
+
+void bdf_beta(int b, double beta[kMaxBdf]) {
+  static const double t[kMaxBdf + 1][kMaxBdf] = {{0, 0, 0, 0},
+                                                 {1.0, 0, 0, 0},
+                                                 {4.0 / 3.0, -1.0 / 3.0, 0, 0},
+                                                 {18.0 / 11.0, -9.0 / 11.0, 2.0 / 11.0, 0},
+                                                 {48.0 / 25.0, -36.0 / 25.0, 16.0 / 25.0, -3.0 / 25.0}};
+  for (int i = 0; i < kMaxBdf; ++i) beta[i] = (b >= 1 && b <= kMaxBdf) ? t[b][i] : 0.0;
+}
+
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags) {
+                            unsigned flags, int bdf_order) {
+  if (bdf_order < 1 || bdf_order > kMaxBdf) return "BDF order out of range";
   hp.m = m; hp.n = n; hp.p = p; hp.alpha = alpha; hp.dt = dt; hp.tol = tol; hp.flags = flags;
+  hp.bdf_order = bdf_order;
   for (int c = 0; c < 2; ++c) {
     hp.Mc[c] = std::max(0, (m - 2 - c + 1) / 2);
     hp.Mfull[c] = (m - c + 1) / 2;
@@ -452,11 +472,11 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
       if (F.size() & 1) F.push_back(0.0);
     }
 
-  for (int kind = 0; kind < 2; ++kind) {
+  for (int kind = 0; kind < kNumKinds; ++kind) {
     KindTables &KT = hp.kind[kind];
     KT = KindTables();
-    if (!(flags & (kind == 0 ? 1u : 2u))) continue;
-    const double ka = (kind == 1) ? alpha * dt : 1.0;   // kappa alpha (heat), 1 (Poisson)
+    if (!(flags & (kind == 0 ? 1u : 2u)) || kind > bdf_order) continue;
+    const double ka = (kind >= 1) ? alpha * dt * bdf_kappa(kind) : 1.0;   // kappa alpha (heat), 1 (Poisson)
     KT.shifts.assign((h + 1) * 2, Shifts());
     // [c, d]: vertical spectrum of Qhat = -(B^-1 D)^T, union over vertical parities
     const double c = -ka * nu_hi, d = -ka * nu_lo;
@@ -464,15 +484,15 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
       for (int pr = 0; pr < 2; ++pr) {
         if (hp.Mc[pr] == 0 || (!both && pr != (k & 1))) continue;
         const double mlo = hp.mu_min[k * 2 + pr], mhi = hp.mu_max[k * 2 + pr];
-        const double a = (kind == 1) ? 1.0 + ka * mlo : mlo;
-        const double b = (kind == 1) ? 1.0 + ka * mhi : mhi;
+        const double a = (kind >= 1) ? 1.0 + ka * mlo : mlo;
+        const double b = (kind >= 1) ? 1.0 + ka * mhi : mhi;
         Shifts &S = KT.shifts[k * 2 + pr];
         if (!zolotarev(a, b, c, d, tol, S)) return "shift computation failed";
         KT.Jmax = std::max(KT.Jmax, S.J);
         const int M = hp.Mc[pr];
         // radial matrices A = -L (Poisson) or C - kappa alpha L (heat)
         Band L = widen(hp.Lblk(k, pr), 2, 3);
-        Band A = (kind == 1) ? axpby(1.0, Cb[pr], -ka, L) : axpby(-1.0, L, 0.0, L);
+        Band A = (kind >= 1) ? axpby(1.0, Cb[pr], -ka, L) : axpby(-1.0, L, 0.0, L);
         const long long roff = (long long)F.size();
         for (int j = 0; j < S.J; ++j) {
           const double pj = S.p[j], qj = S.q[j], s = qj - pj;
@@ -490,7 +510,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
         }
         // transposed radial factors (adjoint of the heat step)
         long long roffT = -1;
-        if (kind == 1) {
+        if (kind >= 1) {
           roffT = (long long)F.size();
           for (int j = 0; j < S.J; ++j) {
             const double pj = S.p[j], qj = S.q[j], s = qj - pj;
@@ -531,7 +551,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             }
           }
           long long zoffT = -1;
-          if (kind == 1) {
+          if (kind >= 1) {
             zoffT = (long long)F.size();
             for (int j = 0; j < S.J; ++j) {
               Band LU = transpose(axpby(1.0, D, S.q[j], Bb[pz]));   // offsets -2 .. 1

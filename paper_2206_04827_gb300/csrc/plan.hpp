@@ -77,7 +77,14 @@ struct Shifts {
   std::vector<double> p, q;   // p in [c,d] (radial solve), q in [a,b] (vertical solve)
 };
 
-struct KindTables {             // one per problem kind (Poisson / heat)
+// Problem kinds: 0 = Poisson, b = 1..4 = one step of the b-th order BDF
+// (kappa^(b) = h * bdf_kappa(b)).
+constexpr int kNumKinds = 5;
+constexpr int kMaxBdf = 4;
+double bdf_kappa(int b);                       // kappa^(b) / h
+void bdf_beta(int b, double beta[kMaxBdf]);    // delta^(b) coefficients (zero-padded)
+
+struct KindTables {             // one per problem kind
   bool built = false;
   // per (k, pr): shifts; index k * 2 + pr
   std::vector<Shifts> shifts;
@@ -94,7 +101,8 @@ struct HostPlan {
   // spectra of the unscaled pencils: mu (radial, per k, parity) and nu (vertical, per parity)
   std::vector<double> mu_min, mu_max;   // index k * 2 + pr
   double nu_min[2] = {0, 0}, nu_max[2] = {0, 0};
-  KindTables kind[2];                   // 0 = Poisson, 1 = heat
+  int bdf_order = 1;                    // highest BDF order built (heat)
+  KindTables kind[kNumKinds];           // 0 = Poisson, 1..bdf_order = BDF 1..b
   std::vector<double> factors;          // all radial and vertical factor rows + rhs bands
   // transform matrices (row-major, out index major): forward and inverse
   std::vector<double> Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i;
@@ -108,7 +116,7 @@ struct HostPlan {
 
 // Build everything on the host.  Returns an empty string on success, else a message.
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags);
+                            unsigned flags, int bdf_order = 1);
 
 double ellip_K(double kprime);
 double jacobi_dn(double u, double kprime);

@@ -30,6 +30,13 @@ _vp = ctypes.c_void_p
 _sig = {
     'cyl_plan': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint, _vp]),
+    'cyl_plan_bdf': (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _vp]),
+    'cyl_heat_step_bdf': (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_longlong, ctypes.c_int, _vp]),
+    'cyl_heat_adjoint_bdf': (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_longlong, ctypes.c_int, _vp,
+                                            ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t]),
+    'cyl_heat_adjoint_bdf_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.POINTER(ctypes.c_size_t)]),
     'cyl_destroy': (ctypes.c_int, [_vp]),
     'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
     'cyl_coeffs2vals': (ctypes.c_int, [_vp, _vp, _vp]),
@@ -107,7 +114,8 @@ class Plan:
     """Owner of one ``cyl_plan_t`` (see include/cyl.h: cyl_plan)."""
 
     def __init__(self, n_r, n_z, n_theta, alpha=0.0, dt=0.0, adi_tol=1e-14, poisson=True, heat=False,
-                 both_parities=False, host_only=False, force_global=False, stream=None, extra_flags=0):
+                 both_parities=False, host_only=False, force_global=False, stream=None, extra_flags=0,
+                 bdf_order=1):
         flags = (WITH_POISSON if poisson else 0) | (WITH_HEAT if heat else 0) \
             | (BOTH_PARITIES if both_parities else 0) | (HOST_ONLY if host_only else 0) \
             | (FORCE_GLOBAL if force_global else 0) | int(extra_flags)
@@ -115,9 +123,11 @@ class Plan:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self._h = _vp()
-        _check(_lib.cyl_plan(ctypes.byref(self._h), int(n_r), int(n_z), int(n_theta), float(alpha), float(dt),
-                             float(adi_tol), flags, _vp(stream) if stream else None), 'cyl_plan')
+        _check(_lib.cyl_plan_bdf(ctypes.byref(self._h), int(n_r), int(n_z), int(n_theta), float(alpha), float(dt),
+                                 float(adi_tol), int(bdf_order), flags, _vp(stream) if stream else None),
+               'cyl_plan_bdf')
         self.m, self.n, self.p = int(n_r), int(n_z), int(n_theta)
+        self.bdf_order = int(bdf_order)
         self.N = self.m * self.n * self.p
         self.alpha, self.dt = float(alpha), float(dt)
 
@@ -160,6 +170,34 @@ class Plan:
                                      int(nsteps), _ptr(bc, 'bc', self.N), _ptr(ckpt, 'ckpt', need),
                                      int(ckpt_every)), 'cyl_heat_step_bc')
         return T
+
+    def heat_step_bdf(self, hist, nvalid, g=None, nsteps=1, g_step_stride=0, bc=None):
+        """nsteps steps of the plan's BDF order on the history hist (bdf_order x N
+        coefficients, slot 0 = newest; include/cyl.h: cyl_heat_step_bdf)."""
+        _check(_lib.cyl_heat_step_bdf(self._h, _ptr(hist, 'hist', self.bdf_order * self.N), int(nvalid),
+                                      _ptr(g, 'g', self.N), int(g_step_stride), int(nsteps),
+                                      _ptr(bc, 'bc', self.N)), 'cyl_heat_step_bdf')
+        return hist
+
+    def heat_adjoint_bdf(self, hist0, nvalid, g, nsteps, dL_dhistN, dL_dhist0, dL_dg=None, dL_dalpha=None,
+                         g_step_stride=0, ckpt_every=1, bc=None, workspace=None):
+        """Reverse-mode gradients of a BDF run (include/cyl.h: cyl_heat_adjoint_bdf).
+        The workspace tensor is allocated here (torch) when not given."""
+        nb = ctypes.c_size_t()
+        _check(_lib.cyl_heat_adjoint_bdf_workspace(self._h, int(nsteps), int(ckpt_every), int(dL_dalpha is not None),
+                                                   ctypes.byref(nb)), 'cyl_heat_adjoint_bdf_workspace')
+        nbytes = nb.value
+        if workspace is None:
+            import torch
+            workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=dL_dhist0.device)
+        bN = self.bdf_order * self.N
+        _check(_lib.cyl_heat_adjoint_bdf(self._h, _ptr(hist0, 'hist0', bN), int(nvalid), _ptr(g, 'g', self.N),
+                                         int(g_step_stride), int(nsteps), _ptr(bc, 'bc', self.N), int(ckpt_every),
+                                         _ptr(dL_dhistN, 'dL_dhistN', bN), _ptr(dL_dhist0, 'dL_dhist0', bN),
+                                         _ptr(dL_dg, 'dL_dg', self.N), _ptr(dL_dalpha, 'dL_dalpha', 1),
+                                         _ptr(workspace, 'workspace', (nbytes + 7) // 8), ctypes.c_size_t(nbytes)),
+               'cyl_heat_adjoint_bdf')
+        return dL_dhist0
 
     def adjoint_workspace_bytes(self, nsteps, ckpt_every, need_alpha):
         nb = ctypes.c_size_t()

@@ -154,3 +154,39 @@ def test_argument_validation(cyl):
         plan.shifts(1, 0, 0)
     assert ei.value.status == cyl.ESTATE
     assert cyl.status_string(cyl.ETIMEOUT).startswith('CYL_ETIMEOUT')
+
+
+def test_bdf_plan_builds_every_order_with_its_kappa(cyl):
+    """A BDF 4 plan holds the step operators of orders 1..4, each the oracle's
+    eq. HelmholtzMatEqn block with kappa = kappa^(b) h (Section 3 BDF
+    definitions), and shifts that make Algorithm 1 converge for each."""
+    from oracle import heat as oheat
+    m, n, p = 20, 18, 8
+    alpha, dt = 0.9, 4e-3
+    plan = cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=False, heat=True, host_only=True, bdf_order=4)
+    rng = np.random.default_rng(6)
+    for b in (1, 2, 3, 4):
+        ka = alpha * dt * float(oheat.bdf_coefficients(b)[0])
+        for k in (0, 3):
+            par = k % 2
+            ms = sy.ModeSystem(m, n, k, 'heat', ka)
+            A, C, B, D = _blocks(ms, par, 0)
+            assert np.allclose(plan.operator(0, b, k, par), A, atol=1e-12 * np.abs(A).max())
+            assert np.allclose(plan.operator(3, b, k, 0), D, atol=1e-12 * max(np.abs(D).max(), 1))
+            J, _, ps, qs = plan.shifts(b, k, par)
+            E = rng.standard_normal((A.shape[0], B.shape[0]))
+            X = _adi(A, B, C, D, E, ps, qs)
+            Xd = sy.solve_kron(A, B, C, D, E)
+            assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max()
+    with pytest.raises(cyl.CylError):
+        plan.shifts(5, 0, 0)
+    plan.close()
+    # a BDF1 plan has no higher-order tables; orders outside 1..4 are rejected
+    p1 = cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=False, heat=True, host_only=True)
+    with pytest.raises(cyl.CylError) as ei:
+        p1.shifts(2, 0, 0)
+    assert ei.value.status == cyl.ESTATE
+    for bad in (0, 5):
+        with pytest.raises(cyl.CylError) as ei:
+            cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=False, heat=True, host_only=True, bdf_order=bad)
+        assert ei.value.status == cyl.EINVAL
