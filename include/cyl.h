@@ -69,6 +69,10 @@ typedef enum {
  * plan time (otherwise the first call with bc != NULL allocates them, which
  * a stream capture does not allow) */
 #define CYL_WITH_BC       64u
+/* plain LU sweeps only: no twisted (two-sided) solves, which otherwise run
+ * where every sweep has at most 128 chains (grids up to about 130); the
+ * results then match the persistent batch kernel bit for bit */
+#define CYL_PLAIN_SWEEPS 128u
 
 /* space selector of cyl_poisson */
 #define CYL_VALUES 0
@@ -86,7 +90,8 @@ typedef enum {
  *   adi_tol    in (0, 1e-2]: target relative accuracy of the Zolotarev bound;
  *              the iteration count per mode is J = ceil(log(16 gamma) log(4/tol) / pi^2).
  *   flags      CYL_WITH_POISSON and/or CYL_WITH_HEAT, optionally
- *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL, CYL_WITH_BC.
+ *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL, CYL_WITH_BC,
+ *              CYL_PLAIN_SWEEPS.
  *   stream     cudaStream_t on which every device call of this plan runs
  *              (NULL = legacy default stream).  Ignored with CYL_HOST_ONLY.
  *
@@ -383,6 +388,17 @@ cyl_status cyl_plan_shifts(cyl_plan_t plan, int which, int k, int parity, int *J
  * block size; out (dim*dim doubles) may be NULL to query the size. */
 cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int parity, int *dim,
                              double *out);
+
+/* Host copy of one work item's factor records for ADI iteration j (the
+ * tables the kernels read; layout in the library's plan header: radial
+ * records of 12 doubles per class row, vertical records of 8 per class
+ * column, plus the interface maps of twisted solves).  info[8] receives
+ * {M, Nz, J, twr, twz, k, parity_r, parity_z}; twr / twz are the split rows of
+ * the twisted radial / vertical solves (0: plain LU sweep).  radial needs
+ * M*12 + (twr ? 24 : 0) doubles, vertical Nz*8 + (twz ? 16 : 0); either may
+ * be NULL.  Items are numbered as the plan lists them (which as above). */
+cyl_status cyl_plan_item_tables(cyl_plan_t plan, int which, int item, int j, int *info, double *radial,
+                                double *vertical);
 
 /* Grid of Definition "grid" (Section 2) into caller-owned HOST arrays:
  * r[m] = cos((m-1-j) pi / (m-1)), z[n] likewise, theta[p] = (2l - p) pi / p.

@@ -28,6 +28,7 @@ struct cyl_plan_s {
   int threads[cyl::kNumKinds] = {};
   size_t smem[cyl::kNumKinds] = {};
   int use_smem[cyl::kNumKinds] = {1, 1, 1, 1, 1};
+  int twist_half[cyl::kNumKinds] = {};   // > 0: the kind's tables hold twisted solves
   int ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
   long long gwork_per_item = 0;
   double *d_gwork = nullptr;
@@ -141,6 +142,7 @@ cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
   a.maxM = P->maxM;
   a.maxNz = P->maxNz;
   a.err = P->d_err;
+  a.twist_half = P->twist_half[kind];
   a.ckpt_every = 1;
   a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
   a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
@@ -338,7 +340,7 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
   if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT))) return CYL_EINVAL;
   if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL |
-                          CYL_TEST_NO_TMA | CYL_WITH_BC))
+                          CYL_TEST_NO_TMA | CYL_WITH_BC | CYL_PLAIN_SWEEPS))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if (bdf_order < 1 || bdf_order > cyl::kMaxBdf) return CYL_EINVAL;
@@ -346,7 +348,8 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   cyl_plan_s *P = new (std::nothrow) cyl_plan_s();
   if (!P) return CYL_ENOMEM;
   try {
-    std::string err = cyl::build_host_plan(P->hp, n_r, n_z, n_theta, alpha, dt, adi_tol, flags, bdf_order);
+    std::string err = cyl::build_host_plan(P->hp, n_r, n_z, n_theta, alpha, dt, adi_tol, flags, bdf_order,
+                                           !(flags & CYL_PLAIN_SWEEPS));
     if (!err.empty()) {
       delete P;
       return CYL_EINVAL;
@@ -372,15 +375,23 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   P->ld = std::max(1, maxW) | 1;
   for (int kind = 0; kind < cyl::kNumKinds; ++kind) {
     int thr = 32;
-    for (const Item &it : h.kind[kind].items) thr = std::max(thr, std::max(it.nsl * it.Nz, it.nsl * it.M));
-    P->threads[kind] = (thr + 31) / 32 * 32;
+    bool tw = false;
+    for (const Item &it : h.kind[kind].items) {
+      thr = std::max(thr, std::max(it.nsl * it.Nz, it.nsl * it.M));
+      tw = tw || it.twr || it.twz;
+    }
+    // twisted solves: one thread per chain and side (top chains in the first half)
+    const int half = (thr + 31) / 32 * 32;
+    P->twist_half[kind] = tw ? half : 0;
+    P->threads[kind] = tw ? 2 * half : half;
+    const int th = P->twist_half[kind];
     int level = 0;
     if (!(flags & CYL_FORCE_GLOBAL)) {
-      if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 2) <= kSmemLimit) level = 2;
-      else if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 1) <= kSmemLimit) level = 1;
+      if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 2, th) <= kSmemLimit) level = 2;
+      else if (cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, 1, th) <= kSmemLimit) level = 1;
     }
     P->use_smem[kind] = level;
-    P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, level);
+    P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, level, th);
   }
   for (int kind = 0; kind < cyl::kNumKinds; ++kind)
     if (P->threads[kind] > 512) {
@@ -822,6 +833,25 @@ cyl_status cyl_plan_shifts(cyl_plan_t P, int which, int k, int parity, int *J, d
   return CYL_OK;
 }
 
+cyl_status cyl_plan_item_tables(cyl_plan_t P, int which, int item, int j, int *info, double *radial,
+                                double *vertical) {
+  if (!P || !info || which < 0 || which >= cyl::kNumKinds || item < 0 || j < 0) return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
+  const auto &KT = P->hp.kind[which];
+  if (!KT.built) return CYL_ESTATE;
+  if (item >= (int)KT.items.size()) return CYL_EINVAL;
+  const Item &it = KT.items[item];
+  if (j >= it.J) return CYL_EINVAL;
+  info[0] = it.M; info[1] = it.Nz; info[2] = it.J; info[3] = it.twr; info[4] = it.twz;
+  info[5] = it.k; info[6] = it.pr; info[7] = it.pz;
+  const size_t rs = (size_t)it.M * cyl::RSTRIDE + (it.twr ? cyl::RTWIST : 0);
+  const size_t zs = (size_t)it.Nz * cyl::ZSTRIDE + (it.twz ? cyl::ZTWIST : 0);
+  const double *F = P->hp.factors.data();
+  if (radial) std::memcpy(radial, F + it.roff + (size_t)j * rs, rs * sizeof(double));
+  if (vertical) std::memcpy(vertical, F + it.zoff + (size_t)j * zs, zs * sizeof(double));
+  return CYL_OK;
+}
+
 cyl_status cyl_plan_operator(cyl_plan_t P, int op, int which, int k, int parity, int *dim, double *out) {
   if (!P || !dim || op < 0 || op > 3 || which < 0 || which >= cyl::kNumKinds || parity < 0 || parity > 1 || k < 0 ||
       k > P->hp.p / 2)
@@ -882,8 +912,9 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
     pool.emplace_back([&, t]() {
       for (int i = t; i < nprob; i += nth) {
         try {
+          // the persistent batch kernel runs plain (untwisted) sweeps
           errs[i] = cyl::build_host_plan(hps[i], n_r[i], n_z[i], n_theta[i], alpha[i], dt, adi_tol,
-                                         (flags & CYL_BOTH_PARITIES) | CYL_WITH_HEAT);
+                                         (flags & CYL_BOTH_PARITIES) | CYL_WITH_HEAT, 1, false);
         } catch (...) {
           errs[i] = "host plan failed";
         }

@@ -25,10 +25,12 @@
 
 namespace cyl {
 
-size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level) {
-  size_t d = 2 * ((size_t)maxM * RSTRIDE + (size_t)maxNz * ZSTRIDE);   // double-buffered factor tables
+size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level, int twist_half) {
+  // double-buffered factor tables (with the interface maps of twisted solves)
+  size_t d = 2 * ((size_t)maxM * RSTRIDE + RTWIST + (size_t)maxNz * ZSTRIDE + ZTWIST);
   if (level >= 1) d += (size_t)smem_rows * ld;                         // iterate S
   if (level >= 2) d += (size_t)maxM * ld;                              // right side Fa
+  d += (size_t)TW_SLOTS * twist_half;                                  // twisted-sweep exchange
   return d * sizeof(double);
 }
 
@@ -263,6 +265,379 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
   }
 }
 
+// ------------------------------------------------------------------ twisted sweeps
+// A banded solve split in two chains that run on two threads (in different
+// warps): LU elimination top-down over rows < k and UL elimination bottom-up
+// over rows > k + w - 1, then a small interface system (rows k .. k+w-1,
+// precomputed map in the table tail), then the two back substitutions
+// outward.  Same FP64 work as one LU sweep, half the chain length, twice the
+// warps: on GB300 a second warp per SM sub-partition lifts the sweep from
+// about 0.80 to about 0.95 of the FP64 pipe.  Records: plan.hpp.  Scratch
+// slots (stride xs_stride): radial 0..1 w_{k-2}, w_{k-1}; 2..4 top partial
+// interface right sides; 5..7 v_{k+3..k+5}; 8..10 bottom partials.
+// Vertical 0 w_{k-1}; 1..2 z_k, z_{k+1}; 3..4 v_{k+2}, v_{k+3}.
+
+// Radial phase 1: top: interface partials (f + apply terms on U rows <= k+2)
+// then forward LU rows 0 .. k-1; bottom: interface partials (apply terms on
+// U rows >= k+3) then forward UL rows M-1 .. k+3.  In place on col.
+template <bool FIRST, int UNR>
+__device__ __forceinline__ void radial_tw1(double *__restrict__ col, const double *__restrict__ Fc, int ld,
+                                           const double *__restrict__ RB, int M, int k, bool bottom,
+                                           double *__restrict__ xs, int xst) {
+  const double2 *rb2 = reinterpret_cast<const double2 *>(RB);
+  if (!bottom) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      double acc = Fc[(k + r) * ld];
+      if (!FIRST) {
+        const double *rec = RB + (k + r) * RSTRIDE;
+#pragma unroll
+        for (int o = -2; o <= 2 - r; ++o) acc = fma(rec[o + 2], col[(k + r + o) * ld], acc);
+      }
+      xs[(2 + r) * xst] = acc;
+    }
+    // forward LU rows 0 .. k-1 (as radial_sweep's first loop, stopped at k)
+    double w[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = 0.0;
+    if (!FIRST) {
+#pragma unroll
+      for (int o = 0; o < 3; ++o) w[2 + o] = col[o * ld];
+    }
+    double fn = Fc[0];
+    double un = FIRST ? 0.0 : col[3 * ld];
+    double2 nrec[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nrec[q] = rb2[q];
+    double y0 = 0.0, y1 = 0.0;
+#pragma unroll UNR
+    for (int i = 0; i < k; ++i) {
+      const double f = fn;
+      double2 rec[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rec[q] = nrec[q];
+      if (!FIRST) w[5] = un;
+      if (i + 1 < k) {
+        fn = Fc[(i + 1) * ld];
+        if (!FIRST) un = col[(i + 4) * ld];
+        const double2 *nx = rb2 + (i + 1) * (RSTRIDE / 2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (!FIRST || q == 3) nrec[q] = nx[q];
+      }
+      double acc = f;
+      if (!FIRST) {
+        acc = fma(comp<0>(rec), w[0], acc);
+        acc = fma(comp<1>(rec), w[1], acc);
+        acc = fma(comp<2>(rec), w[2], acc);
+        acc = fma(comp<3>(rec), w[3], acc);
+        acc = fma(comp<4>(rec), w[4], acc);
+        acc = fma(comp<5>(rec), w[5], acc);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) w[q] = w[q + 1];
+      }
+      acc = fma(comp<7>(rec), y1, acc);
+      acc = fma(comp<6>(rec), y0, acc);
+      col[i * ld] = acc;
+      y1 = y0;
+      y0 = acc;
+    }
+    xs[0] = y1;          // w_{k-2}
+    xs[xst] = y0;        // w_{k-1}
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      double acc = 0.0;
+      if (!FIRST) {
+        const double *rec = RB + (k + r) * RSTRIDE;
+#pragma unroll
+        for (int o = 3 - r; o <= 3; ++o) acc = fma(rec[o + 2], col[(k + r + o) * ld], acc);
+      }
+      xs[(8 + r) * xst] = acc;
+    }
+    // forward UL rows M-1 .. k+3; wv holds the original U_{i-2} .. U_{i+3}
+    double wv[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wv[q] = 0.0;
+    if (!FIRST) {
+      wv[0] = col[(M - 3) * ld];
+      wv[1] = col[(M - 2) * ld];
+      wv[2] = col[(M - 1) * ld];
+    }
+    double fn = Fc[(M - 1) * ld];
+    double un = FIRST ? 0.0 : col[(M - 4) * ld];
+    double2 nrec[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) nrec[q] = rb2[(M - 1) * (RSTRIDE / 2) + q];
+    double v1 = 0.0, v2 = 0.0, v3 = 0.0;      // v_{i+1}, v_{i+2}, v_{i+3}
+#pragma unroll UNR
+    for (int i = M - 1; i >= k + 3; --i) {
+      const double f = fn;
+      double2 rec[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) rec[q] = nrec[q];
+      const double unext = un;
+      if (i - 1 >= k + 3) {
+        fn = Fc[(i - 1) * ld];
+        if (!FIRST) un = col[(i - 4) * ld];
+        const double2 *nx = rb2 + (i - 1) * (RSTRIDE / 2);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+          if (!FIRST || q >= 3) nrec[q] = nx[q];
+      }
+      double acc = f;
+      if (!FIRST) {
+        acc = fma(comp<5>(rec), wv[5], acc);
+        acc = fma(comp<4>(rec), wv[4], acc);
+        acc = fma(comp<3>(rec), wv[3], acc);
+        acc = fma(comp<2>(rec), wv[2], acc);
+        acc = fma(comp<1>(rec), wv[1], acc);
+        acc = fma(comp<0>(rec), wv[0], acc);
+#pragma unroll
+        for (int q = 5; q > 0; --q) wv[q] = wv[q - 1];
+        wv[0] = unext;
+      }
+      acc = fma(comp<8>(rec), v3, acc);
+      acc = fma(comp<7>(rec), v2, acc);
+      acc = fma(comp<6>(rec), v1, acc);
+      col[i * ld] = acc;
+      v3 = v2;
+      v2 = v1;
+      v1 = acc;
+    }
+    xs[5 * xst] = v1;    // v_{k+3}
+    xs[6 * xst] = v2;    // v_{k+4}
+    xs[7 * xst] = v3;    // v_{k+5}
+  }
+}
+
+// Radial phase 2: interface unknowns z_k .. z_{k+2} from the 3 x 8 map (both
+// threads, from scratch), then the back substitutions outward.
+template <int UNR>
+__device__ __forceinline__ void radial_tw2(double *__restrict__ col, int ld, const double *__restrict__ RB, int M,
+                                           int k, bool bottom, const double *__restrict__ xs, int xst) {
+  const double *R = RB + M * RSTRIDE;
+  double rhs[8];
+  rhs[0] = xs[0];
+  rhs[1] = xs[xst];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rhs[2 + r] = xs[(2 + r) * xst] + xs[(8 + r) * xst];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rhs[5 + r] = xs[(5 + r) * xst];
+  double zI[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = fma(R[o * 8 + q], rhs[q], s);
+    zI[o] = s;
+  }
+  const double2 *rb2 = reinterpret_cast<const double2 *>(RB);
+  if (!bottom) {
+#pragma unroll
+    for (int o = 0; o < 3; ++o) col[(k + o) * ld] = zI[o];
+    // back substitution rows k-1 .. 0 (LU records [8..11])
+    double z0 = zI[0], z1 = zI[1], z2 = zI[2];
+    double yn = col[(k - 1) * ld];
+    double2 nb[2];
+    nb[0] = rb2[(k - 1) * (RSTRIDE / 2) + 4];
+    nb[1] = rb2[(k - 1) * (RSTRIDE / 2) + 5];
+#pragma unroll UNR
+    for (int i = k - 1; i >= 0; --i) {
+      const double yv = yn;
+      const double2 c0 = nb[0], c1 = nb[1];
+      if (i > 0) {
+        yn = col[(i - 1) * ld];
+        nb[0] = rb2[(i - 1) * (RSTRIDE / 2) + 4];
+        nb[1] = rb2[(i - 1) * (RSTRIDE / 2) + 5];
+      }
+      double acc = c1.y * yv;                 // (q-p)/U_ii
+      acc = fma(c1.x, z2, acc);               // -U[i][i+3]/U_ii
+      acc = fma(c0.y, z1, acc);               // -U[i][i+2]/U_ii
+      const double zi = fma(c0.x, z0, acc);   // -U[i][i+1]/U_ii
+      col[i * ld] = zi;
+      z2 = z1;
+      z1 = z0;
+      z0 = zi;
+    }
+  } else {
+    // forward substitution rows k+3 .. M-1 (UL records [9..11])
+    double zm1 = zI[2], zm2 = zI[1];
+    double vn = col[(k + 3) * ld];
+    double2 nb[2];
+    nb[0] = rb2[(k + 3) * (RSTRIDE / 2) + 4];
+    nb[1] = rb2[(k + 3) * (RSTRIDE / 2) + 5];
+#pragma unroll UNR
+    for (int i = k + 3; i < M; ++i) {
+      const double vv = vn;
+      const double2 c0 = nb[0], c1 = nb[1];
+      if (i + 1 < M) {
+        vn = col[(i + 1) * ld];
+        nb[0] = rb2[(i + 1) * (RSTRIDE / 2) + 4];
+        nb[1] = rb2[(i + 1) * (RSTRIDE / 2) + 5];
+      }
+      double acc = c1.y * vv;                 // (q-p)/Lt_ii
+      acc = fma(c1.x, zm2, acc);              // -Lt[i][i-2]/Lt_ii
+      const double zi = fma(c0.y, zm1, acc);  // -Lt[i][i-1]/Lt_ii
+      col[i * ld] = zi;
+      zm2 = zm1;
+      zm1 = zi;
+    }
+  }
+}
+
+// Vertical phase 1: top: save z_k, z_{k+1}, forward LU columns 0 .. k-1;
+// bottom: forward UL columns Nz-1 .. k+2.  In place on row.
+template <int UNR>
+__device__ __forceinline__ void vertical_tw1(double *__restrict__ row, const double *__restrict__ ZB, int Nz, int k,
+                                             bool bottom, double *__restrict__ xs, int xst) {
+  const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
+  if (!bottom) {
+    xs[xst] = row[k];
+    xs[2 * xst] = row[k + 1];
+    double wq = 0.0;
+    double rn = row[0];
+    double2 cn = z2p[0];
+#pragma unroll UNR
+    for (int b = 0; b < k; ++b) {
+      const double r = rn;
+      const double2 cc = cn;
+      if (b + 1 < k) {
+        rn = row[b + 1];
+        cn = z2p[(b + 1) * 4];
+      }
+      const double w = fma(cc.x, wq, r);
+      row[b] = w;
+      wq = w;
+    }
+    xs[0] = wq;          // w_{k-1}
+  } else {
+    double v1 = 0.0, v2 = 0.0;
+    double rn = row[Nz - 1];
+    double2 cn = z2p[(Nz - 1) * 4];
+#pragma unroll UNR
+    for (int b = Nz - 1; b >= k + 2; --b) {
+      const double r = rn;
+      const double2 cc = cn;
+      if (b - 1 >= k + 2) {
+        rn = row[b - 1];
+        cn = z2p[(b - 1) * 4];
+      }
+      const double v = fma(cc.x, v1, fma(cc.y, v2, r));   // -Ut[b][b+1], -Ut[b][b+2]
+      row[b] = v;
+      v2 = v1;
+      v1 = v;
+    }
+    xs[3 * xst] = v1;    // v_{k+2}
+    xs[4 * xst] = v2;    // v_{k+3}
+  }
+}
+
+// Vertical phase 2: interface x_k .. x_{k+2} from the 3 x 5 map, back
+// substitutions outward and (unless LAST) the next iteration's apply band
+// u = (D + p'B) x: the top thread writes u_0 .. u_k, the bottom u_{k+1} ..
+template <bool LAST, int UNR>
+__device__ __forceinline__ void vertical_tw2(double *__restrict__ row, const double *__restrict__ ZB, int Nz, int k,
+                                             bool bottom, const double *__restrict__ xs, int xst) {
+  const double *R = ZB + Nz * ZSTRIDE;
+  double rhs[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) rhs[q] = xs[q * xst];
+  double xI[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s = fma(R[o * 5 + q], rhs[q], s);
+    xI[o] = s;
+  }
+  const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
+  if (!bottom) {
+    double x1 = xI[0], x2 = xI[1], x3 = xI[2];            // x_{b+1}, x_{b+2}, x_{b+3}
+    if (LAST) {
+      row[k] = xI[0];
+      row[k + 1] = xI[1];
+    }
+    double2 q45 = z2p[k * 4 + 2], q67 = z2p[k * 4 + 3];    // apply record of column b+1
+    double wn = row[k - 1];
+    double2 p01 = z2p[(k - 1) * 4], p23 = z2p[(k - 1) * 4 + 1], p45, p67;
+    if (!LAST) { p45 = z2p[(k - 1) * 4 + 2]; p67 = z2p[(k - 1) * 4 + 3]; }
+#pragma unroll UNR
+    for (int b = k - 1; b >= 0; --b) {
+      const double wb = wn;
+      const double2 c01 = p01, c23 = p23;
+      double2 c45, c67;
+      if (!LAST) { c45 = p45; c67 = p67; }
+      if (b > 0) {
+        wn = row[b - 1];
+        p01 = z2p[(b - 1) * 4];
+        p23 = z2p[(b - 1) * 4 + 1];
+        if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
+      }
+      const double v = fma(c23.x, x2, c23.y * wb);
+      const double xb = fma(c01.y, x1, v);
+      if (LAST) {
+        row[b] = xb;
+      } else {
+        double u = q67.y * x3;
+        u = fma(q67.x, x2, u);
+        u = fma(q45.y, x1, u);
+        u = fma(q45.x, xb, u);
+        row[b + 1] = u;
+        q45 = c45;
+        q67 = c67;
+      }
+      x3 = x2;
+      x2 = x1;
+      x1 = xb;
+    }
+    if (!LAST) {
+      double u = q45.y * x1;                 // column 0: x_{-1} = 0
+      u = fma(q67.x, x2, u);
+      u = fma(q67.y, x3, u);
+      row[0] = u;
+    }
+  } else {
+    double xm3 = 0.0, xm2 = xI[0], xm1 = xI[1];            // x_{b-3}, x_{b-2}, x_{b-1}
+    double vn = row[k + 2];
+    double2 p23 = z2p[(k + 2) * 4 + 1];
+#pragma unroll UNR
+    for (int b = k + 2; b < Nz; ++b) {
+      const double vb = vn;
+      const double2 c23 = p23;
+      if (b + 1 < Nz) {
+        vn = row[b + 1];
+        p23 = z2p[(b + 1) * 4 + 1];
+      }
+      const double xb = fma(c23.x, xm1, c23.y * vb);       // -Lt[b][b-1]/Lt_bb, 1/Lt_bb
+      if (LAST) {
+        row[b] = xb;
+      } else if (b >= k + 3) {
+        const double2 a45 = z2p[(b - 2) * 4 + 2], a67 = z2p[(b - 2) * 4 + 3];
+        double u = a67.y * xb;
+        u = fma(a67.x, xm1, u);
+        u = fma(a45.y, xm2, u);
+        u = fma(a45.x, xm3, u);
+        row[b - 2] = u;
+      }
+      xm3 = xm2;
+      xm2 = xm1;
+      xm1 = xb;
+    }
+    if (!LAST) {                              // columns Nz-2, Nz-1 (x_{Nz}, x_{Nz+1} = 0)
+      const double2 a45 = z2p[(Nz - 2) * 4 + 2], a67 = z2p[(Nz - 2) * 4 + 3];
+      double u = a67.x * xm1;
+      u = fma(a45.y, xm2, u);
+      u = fma(a45.x, xm3, u);
+      row[Nz - 2] = u;
+      const double2 b45 = z2p[(Nz - 1) * 4 + 2];
+      double u1 = b45.y * xm1;
+      u1 = fma(b45.x, xm2, u1);
+      row[Nz - 1] = u1;
+    }
+  }
+}
+
 // A group of threads that processes one item: the whole CTA (named barrier 0)
 // or one of G equal slices of it (named barriers 1 .. G).
 struct Grp {
@@ -281,18 +656,22 @@ struct AdiShared {
   double *RB0, *ZB0;
   int rlen, zlen;
   unsigned long long *bar;
+  double *xs;     // twisted-sweep exchange scratch (TW_SLOTS x xhalf doubles), or NULL
+  int xhalf;      // threads per side of a twisted sweep (half the group)
 };
 
 template <bool TRANS>
 __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs &a, const Item &it, long long c,
                                              long long c0) {
   const int jt = (int)((c - c0) % it.J), buf = (int)(c & 1);
-  const unsigned rbytes = (unsigned)(it.M * RSTRIDE * sizeof(double));
-  const unsigned zbytes = (unsigned)(it.Nz * ZSTRIDE * sizeof(double));
+  const int rsz = it.M * RSTRIDE + ((!TRANS && it.twr) ? RTWIST : 0);
+  const int zsz = it.Nz * ZSTRIDE + ((!TRANS && it.twz) ? ZTWIST : 0);
+  const unsigned rbytes = (unsigned)(rsz * sizeof(double));
+  const unsigned zbytes = (unsigned)(zsz * sizeof(double));
   const long long roff = TRANS ? it.roffT : it.roff, zoff = TRANS ? it.zoffT : it.zoff;
   mbar_expect(&sh.bar[buf], rbytes + zbytes);
-  bulk_g2s(sh.RB0 + buf * sh.rlen, a.fac + roff + (size_t)jt * it.M * RSTRIDE, rbytes, &sh.bar[buf]);
-  bulk_g2s(sh.ZB0 + buf * sh.zlen, a.fac + zoff + (size_t)jt * it.Nz * ZSTRIDE, zbytes, &sh.bar[buf]);
+  bulk_g2s(sh.RB0 + buf * sh.rlen, a.fac + roff + (size_t)jt * rsz, rbytes, &sh.bar[buf]);
+  bulk_g2s(sh.ZB0 + buf * sh.zlen, a.fac + zoff + (size_t)jt * zsz, zbytes, &sh.bar[buf]);
 }
 
 // UNR: unroll factor of the sweeps.  Measured on GB300: 2 with the work
@@ -312,15 +691,38 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1), a.wait_limit)) timed_out = true;
     const double *RB = sh.RB0 + buf * sh.rlen;
     const double *ZB = sh.ZB0 + buf * sh.zlen;
-    for (int col = gp.tid; col < W; col += gp.nth) {
-      if (jt == 0) radial_sweep<true, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
-      else radial_sweep<false, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
+    const int xh = sh.xhalf;
+    const bool bottom = gp.tid >= xh;
+    const int chain = gp.tid - (bottom ? xh : 0);
+    if (!TRANS && it.twr) {
+      if (chain < W) {
+        if (jt == 0) radial_tw1<true, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+        else radial_tw1<false, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+      }
+      gp.sync();
+      if (chain < W) radial_tw2<UNR>(S + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+    } else {
+      for (int col = gp.tid; col < W; col += gp.nth) {
+        if (jt == 0) radial_sweep<true, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
+        else radial_sweep<false, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
+      }
     }
     gp.sync();
-    for (int r = gp.tid; r < nsl * M; r += gp.nth) {
-      const int sl = r / M, aa = r - sl * M;
-      if (jt + 1 == J) vertical_sweep<true, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
-      else vertical_sweep<false, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+    if (!TRANS && it.twz) {
+      const int sl = chain / M, aa = chain - sl * M;
+      double *rowp = S + aa * ld + sl * Nz;
+      if (chain < nsl * M) vertical_tw1<UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+      gp.sync();
+      if (chain < nsl * M) {
+        if (jt + 1 == J) vertical_tw2<true, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+        else vertical_tw2<false, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+      }
+    } else {
+      for (int r = gp.tid; r < nsl * M; r += gp.nth) {
+        const int sl = r / M, aa = r - sl * M;
+        if (jt + 1 == J) vertical_sweep<true, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+        else vertical_sweep<false, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+      }
     }
     gp.sync();
   }
@@ -458,8 +860,8 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   const Item it = a.items[blockIdx.x];
   const Grp gp{(int)threadIdx.x, (int)blockDim.x, 0};
   AdiShared sh;
-  sh.rlen = a.maxM * RSTRIDE;
-  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.rlen = a.maxM * RSTRIDE + RTWIST;
+  sh.zlen = a.maxNz * ZSTRIDE + ZTWIST;
   sh.RB0 = sm;
   sh.ZB0 = sm + 2 * sh.rlen;
   sh.bar = bar;
@@ -468,6 +870,9 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   double *S = S_SMEM ? smem_next : gw;
   if (S_SMEM) smem_next += (size_t)a.smem_rows * a.ld;
   double *Fa = F_SMEM ? smem_next : gw + (S_SMEM ? 0 : (size_t)a.smem_rows * a.ld);
+  if (F_SMEM) smem_next += (size_t)a.maxM * a.ld;
+  sh.xs = a.twist_half ? smem_next : nullptr;
+  sh.xhalf = a.twist_half ? a.twist_half : gp.nth;
   init_bars(gp, bar);
   bool timed_out = false;
   long long c = 0;
@@ -495,6 +900,8 @@ __global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int 
   sh.RB0 = base;
   sh.ZB0 = base + 2 * sh.rlen;
   sh.bar = bar + 2 * g;
+  sh.xs = nullptr;        // batch items are never twisted
+  sh.xhalf = gsize;
   double *S = sh.ZB0 + 2 * sh.zlen;
   double *Fa = a.gwork + ((size_t)blockIdx.x * G + g) * a.gwork_per_item;
   init_bars(gp, sh.bar);
@@ -570,6 +977,8 @@ __global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, Ad
   sh.RB0 = sm;
   sh.ZB0 = sm + 2 * sh.rlen;
   sh.bar = bar;
+  sh.xs = nullptr;        // the transposed tables are never twisted
+  sh.xhalf = nth;
   double *S = SMEM ? sh.ZB0 + 2 * sh.zlen : a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
   double *Fa = S + (size_t)a.smem_rows * ld;
   const Grp gp{tid, nth, 0};
@@ -842,19 +1251,22 @@ static cudaError_t launch_adi_t(const AdiArgs &a, int threads, size_t smem, cuda
   return cudaGetLastError();
 }
 
-// Blocks of at most 128 threads get an instantiation with a larger register
-// budget (up to 255 per thread).
+// Blocks of at most 128 and 256 threads (plain and twisted sweeps of grids up
+// to about 130) get instantiations with a register budget of 255 per thread.
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
-  const bool small = threads <= 128;
+  const int t = threads <= 128 ? 128 : (threads <= 256 ? 256 : 512);
   if (a.use_smem == 2)
-    return small ? launch_adi_t<true, true, 128>(a, threads, smem, st)
-                 : launch_adi_t<true, true, 512>(a, threads, smem, st);
+    return t == 128 ? launch_adi_t<true, true, 128>(a, threads, smem, st)
+           : t == 256 ? launch_adi_t<true, true, 256>(a, threads, smem, st)
+                      : launch_adi_t<true, true, 512>(a, threads, smem, st);
   if (a.use_smem == 1)
-    return small ? launch_adi_t<true, false, 128>(a, threads, smem, st)
-                 : launch_adi_t<true, false, 512>(a, threads, smem, st);
-  return small ? launch_adi_t<false, false, 128>(a, threads, smem, st)
-               : launch_adi_t<false, false, 512>(a, threads, smem, st);
+    return t == 128 ? launch_adi_t<true, false, 128>(a, threads, smem, st)
+           : t == 256 ? launch_adi_t<true, false, 256>(a, threads, smem, st)
+                      : launch_adi_t<true, false, 512>(a, threads, smem, st);
+  return t == 128 ? launch_adi_t<false, false, 128>(a, threads, smem, st)
+         : t == 256 ? launch_adi_t<false, false, 256>(a, threads, smem, st)
+                    : launch_adi_t<false, false, 512>(a, threads, smem, st);
 }
 
 __global__ void axis_matvec_kernel(const double *__restrict__ in, double *__restrict__ out,

@@ -41,6 +41,7 @@ struct AdiArgs {
   long long hist_stride;
   int hist_b, hist_base, order;
   double beta[4];
+  int twist_half;          // > 0: twisted sweeps, threads [0, h) top chains, [h, 2h) bottom chains
   const double *lift;      // coefficients of the lifting W of the boundary data, or NULL
   const double *corr;      // right-side correction of the lifted problem (class positions), or NULL
   int test_no_tma;         // failure-detection test: never start table copies, so waits run out
@@ -82,7 +83,8 @@ cudaError_t launch_permute_slots(double *dst, const double *src, long long N, in
                                  cudaStream_t st);
 cudaError_t launch_sum_partials(const double *part, int n, double scale, double *out, cudaStream_t st);
 
-size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level);
+constexpr int TW_SLOTS = 11;   // exchange doubles per chain of a twisted sweep
+size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level, int twist_half);
 size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz);
 size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz);
 cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int blocks, size_t smem,

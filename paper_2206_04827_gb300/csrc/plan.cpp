@@ -126,6 +126,80 @@ void lu_solve(const Band &LU, std::vector<double> &x) {
   }
 }
 
+// UL factorization without pivoting, eliminating from the bottom up:
+// A = Ut Lt with Ut unit upper (its multipliers stored in the strict upper
+// band) and Lt lower (stored on and below the diagonal).
+bool ul_inplace(Band &A) {
+  for (int c = A.n - 1; c >= 0; --c) {
+    const double piv = A.get(c, c);
+    if (!(std::fabs(piv) > 0.0) || !std::isfinite(piv)) return false;
+    for (int r = c - 1; r >= std::max(0, c - A.hi); --r) {
+      const double u = A.get(r, c) / piv;
+      A.at(r, c) = u;
+      for (int j = std::max(0, c - A.lo); j < c; ++j)
+        if (A.in(r, j)) A.at(r, j) -= u * A.get(c, j);
+    }
+  }
+  return true;
+}
+
+// Solve the dense n x n system K X = B (row-major, B n x nr) in place by
+// Gaussian elimination with partial pivoting; false if K is singular.
+static bool dense_solve(std::vector<double> K, int n, std::vector<double> &B, int nr) {
+  for (int c = 0; c < n; ++c) {
+    int pv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(K[r * n + c]) > std::fabs(K[pv * n + c])) pv = r;
+    if (!(std::fabs(K[pv * n + c]) > 0.0)) return false;
+    if (pv != c) {
+      for (int j = 0; j < n; ++j) std::swap(K[c * n + j], K[pv * n + j]);
+      for (int j = 0; j < nr; ++j) std::swap(B[c * nr + j], B[pv * nr + j]);
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const double f = K[r * n + c] / K[c * n + c];
+      if (f == 0.0) continue;
+      for (int j = c; j < n; ++j) K[r * n + j] -= f * K[c * n + j];
+      for (int j = 0; j < nr; ++j) B[r * nr + j] -= f * B[c * nr + j];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c)
+    for (int j = 0; j < nr; ++j) {
+      double s = B[c * nr + j];
+      for (int l = c + 1; l < n; ++l) s -= K[c * n + l] * B[l * nr + j];
+      B[c * nr + j] = s / K[c * n + c];
+    }
+  return true;
+}
+
+// Interface block of a twisted banded solve T z = s * rhs (s = scale): the
+// top rows are LU rows (U z = s w), the bottom rows UL rows (Lt z = s v).
+// Unknowns z_{k-lo} .. z_{k+w+hi-1} (w = max(lo, hi) interface rows k ..
+// k+w-1); equations: U rows k-lo .. k-1, T rows k .. k+w-1, Lt rows k+w ..
+// k+w+hi-1.  Returns the rows of the solution map for z_k .. z_{k+nout-1}
+// (nout x neq, row-major), scaled by s.
+static bool twist_interface(const Band &T, const Band &LU, const Band &UL, int k, int nout, double s,
+                            std::vector<double> &R) {
+  const int lo = T.lo, hi = T.hi, w = std::max(lo, hi), n0 = k - lo, neq = lo + w + hi;
+  std::vector<double> K((size_t)neq * neq, 0.0), E((size_t)neq * neq, 0.0);
+  for (int r = 0; r < neq; ++r) {
+    const int i = n0 + r;
+    for (int cidx = 0; cidx < neq; ++cidx) {
+      const int j = n0 + cidx;
+      double v;
+      if (r < lo) v = (j >= i) ? LU.get(i, j) : 0.0;          // U row
+      else if (r < lo + w) v = T.get(i, j);                   // equation row
+      else v = (j <= i) ? UL.get(i, j) : 0.0;                 // Lt row
+      K[(size_t)r * neq + cidx] = v;
+    }
+    E[(size_t)r * neq + r] = 1.0;
+  }
+  if (!dense_solve(K, neq, E, neq)) return false;             // E = K^-1
+  R.assign((size_t)nout * neq, 0.0);
+  for (int o = 0; o < nout; ++o)
+    for (int cidx = 0; cidx < neq; ++cidx) R[(size_t)o * neq + cidx] = s * E[(size_t)(lo + o) * neq + cidx];
+  return true;
+}
+
 std::vector<double> matvec(const Band &A, const std::vector<double> &x) {
   std::vector<double> y(A.n, 0.0);
   for (int i = 0; i < A.n; ++i)
@@ -383,7 +457,7 @@ void bdf_beta(int b, double beta[kMaxBdf]) {
 }
 
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags, int bdf_order) {
+                            unsigned flags, int bdf_order, bool twist) {
   if (bdf_order < 1 || bdf_order > kMaxBdf) return "BDF order out of range";
   hp.m = m; hp.n = n; hp.p = p; hp.alpha = alpha; hp.dt = dt; hp.tol = tol; hp.flags = flags;
   hp.bdf_order = bdf_order;
@@ -472,6 +546,10 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
       if (F.size() & 1) F.push_back(0.0);
     }
 
+  // twisted solves only where both sweeps' chains (two slices x class size) fit kTwistMaxChains:
+  // there the second half of the threads doubles the warps per SM sub-partition
+  const bool tw_ok = twist && 2 * std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1])) <=
+                                  kTwistMaxChains;
   for (int kind = 0; kind < kNumKinds; ++kind) {
     KindTables &KT = hp.kind[kind];
     KT = KindTables();
@@ -494,18 +572,40 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
         Band L = widen(hp.Lblk(k, pr), 2, 3);
         Band A = (kind >= 1) ? axpby(1.0, Cb[pr], -ka, L) : axpby(-1.0, L, 0.0, L);
         const long long roff = (long long)F.size();
+        const int kr = (tw_ok && M >= kTwistMinM) ? (M - 3) / 2 : 0;   // twisted split of the radial solve
         for (int j = 0; j < S.J; ++j) {
           const double pj = S.p[j], qj = S.q[j], s = qj - pj;
           Band LU = axpby(1.0, A, -pj, Cb[pr]);
           if (!lu_inplace(LU)) return "radial LU failed (zero pivot)";
+          Band UL;
+          if (kr) {
+            UL = axpby(1.0, A, -pj, Cb[pr]);
+            if (!ul_inplace(UL)) return "radial UL failed (zero pivot)";
+          }
           for (int i = 0; i < M; ++i) {
             for (int o = -2; o <= 3; ++o)
               F.push_back((i + o >= 0 && i + o < M) ? (A.get(i, i + o) - qj * Cb[pr].get(i, i + o)) / s : 0.0);
-            F.push_back(i >= 1 ? -LU.get(i, i - 1) : 0.0);
-            F.push_back(i >= 2 ? -LU.get(i, i - 2) : 0.0);
-            const double dpiv = s / LU.get(i, i);
-            for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
-            F.push_back(dpiv);
+            if (kr == 0 || i < kr) {            // LU row (top of a twisted solve)
+              F.push_back(i >= 1 ? -LU.get(i, i - 1) : 0.0);
+              F.push_back(i >= 2 ? -LU.get(i, i - 2) : 0.0);
+              const double dpiv = s / LU.get(i, i);
+              for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
+              F.push_back(dpiv);
+            } else if (i < kr + 3) {            // interface row: apply band only
+              for (int o = 0; o < 6; ++o) F.push_back(0.0);
+            } else {                            // UL row (bottom of a twisted solve)
+              for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -UL.get(i, i + o) : 0.0);
+              const double dpiv = s / UL.get(i, i);
+              F.push_back(-UL.get(i, i - 1) / s * dpiv);
+              F.push_back(-UL.get(i, i - 2) / s * dpiv);
+              F.push_back(dpiv);
+            }
+          }
+          if (kr) {                             // interface map (3 x 8), scaled by q - p
+            Band T = axpby(1.0, A, -pj, Cb[pr]);
+            std::vector<double> R;
+            if (!twist_interface(T, LU, UL, kr, 3, s, R)) return "radial interface solve failed";
+            F.insert(F.end(), R.begin(), R.end());
           }
         }
         // transposed radial factors (adjoint of the heat step)
@@ -533,21 +633,44 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
           if (Nz == 0) continue;
           Band D = axpby(-ka, D2b[pz], 0.0, D2b[pz]);
           const long long zoff = (long long)F.size();
+          const int kz = (tw_ok && Nz >= kTwistMinN) ? (Nz - 2) / 2 : 0;   // twisted split of the vertical solve
           for (int j = 0; j < S.J; ++j) {
-            Band LU = axpby(1.0, D, S.q[j], Bb[pz]);
+            Band T = axpby(1.0, D, S.q[j], Bb[pz]);
+            Band LU = T;
             if (!lu_inplace(LU)) return "vertical LU failed (zero pivot)";
+            Band UL;
+            if (kz) {
+              UL = T;
+              if (!ul_inplace(UL)) return "vertical UL failed (zero pivot)";
+            }
             const bool last = (j + 1 == S.J);
             const double pn = last ? 0.0 : S.p[j + 1];
             for (int cc = 0; cc < Nz; ++cc) {
-              const double dz = 1.0 / LU.get(cc, cc);
-              F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
-              F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
-              F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) * dz : 0.0);
-              F.push_back(dz);
+              if (kz == 0 || cc < kz) {         // LU column (top of a twisted solve)
+                const double dz = 1.0 / LU.get(cc, cc);
+                F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
+                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
+                F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) * dz : 0.0);
+                F.push_back(dz);
+              } else if (cc < kz + 2) {         // interface column: apply band only
+                for (int o = 0; o < 4; ++o) F.push_back(0.0);
+              } else {                          // UL column (bottom of a twisted solve)
+                const double dz = 1.0 / UL.get(cc, cc);
+                F.push_back(cc + 1 < Nz ? -UL.get(cc, cc + 1) : 0.0);
+                F.push_back(cc + 2 < Nz ? -UL.get(cc, cc + 2) : 0.0);
+                F.push_back(-UL.get(cc, cc - 1) * dz);
+                F.push_back(dz);
+              }
               for (int o = -1; o <= 2; ++o) {
                 const int l = cc + o;
                 F.push_back((!last && l >= 0 && l < Nz) ? D.get(cc, l) + pn * Bb[pz].get(cc, l) : 0.0);
               }
+            }
+            if (kz) {                           // interface map (3 x 5), padded to 16
+              std::vector<double> R;
+              if (!twist_interface(T, LU, UL, kz, 3, 1.0, R)) return "vertical interface solve failed";
+              F.insert(F.end(), R.begin(), R.end());
+              F.push_back(0.0);
             }
           }
           long long zoffT = -1;
@@ -580,6 +703,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             it.roffT = roffT; it.zoffT = zoffT;
             it.m = m; it.n = n; it.xoff = 0;
             it.lkoff = lkoff[k * 2 + pr]; it.d2off = d2off[pz];
+            it.twr = kr; it.twz = kz;
             KT.items.push_back(it);
           };
           if (k == 0) add_item(0, 1);

@@ -48,6 +48,21 @@ constexpr int RSTRIDE = 12;
 constexpr int ZSTRIDE = 8;
 // Right-hand-side bands: R_2[i][i+2s] (s = -1..3) per radial class row and
 // C02[j][j+2t] (t = 0..2) per vertical class column.
+// Twisted solves (forward tables only).  With split row k the radial table
+// holds LU records for rows < k, apply-only records for the interface rows
+// k .. k+2, and UL records for rows > k+2:
+//   [0..5] apply band as above, [6..8] -Ut[i][i+1..i+3] (unit upper of
+//   A - pC = Ut Lt), [9..10] -Lt[i][i-1], -Lt[i][i-2] over Lt[i][i], [11] (q-p)/Lt[i][i],
+// followed by RTWIST doubles: the 3 x 8 map from (w_{k-2}, w_{k-1}, y_k,
+// y_{k+1}, y_{k+2}, v_{k+3}, v_{k+4}, v_{k+5}) to z_k .. z_{k+2}.  The vertical
+// table (split column k) holds LU records for columns < k, apply-only for
+// k, k+1, and UL records [0..1] -Ut[c][c+1..c+2], [2] -Lt[c][c-1]/Lt[c][c],
+// [3] 1/Lt[c][c] beyond, followed by ZTWIST doubles: the 3 x 5 map from
+// (w_{k-1}, z_k, z_{k+1}, v_{k+2}, v_{k+3}) to x_k .. x_{k+2} (one pad).
+constexpr int RTWIST = 24;
+constexpr int ZTWIST = 16;
+constexpr int kTwistMinM = 10, kTwistMinN = 8;
+constexpr int kTwistMaxChains = 128;
 constexpr int R2STRIDE = 5;
 constexpr int C02STRIDE = 3;
 
@@ -69,6 +84,7 @@ struct Item {
   long long zoffT;    // transposed vertical factors (adjoint), heat only, else -1
   long long lkoff;    // radial operator L_k bands [M][3] (lifting of boundary data)
   long long d2off;    // vertical D2 band [Nz] (lifting of boundary data)
+  int twr, twz;       // twisted split rows of the radial / vertical solves (0: plain)
 };
 
 struct Shifts {
@@ -115,8 +131,10 @@ struct HostPlan {
 };
 
 // Build everything on the host.  Returns an empty string on success, else a message.
+// twist: allow twisted (two-sided) solves where both sweeps' chain counts fit
+// 128 threads (see kTwistMaxChains); batch plans pass false.
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags, int bdf_order = 1);
+                            unsigned flags, int bdf_order = 1, bool twist = true);
 
 double ellip_K(double kprime);
 double jacobi_dn(double u, double kprime);

@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # status codes and flags (include/cyl.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA, WITH_BC = 1, 2, 4, 8, 16, 32, 64
+PLAIN_SWEEPS = 128
 VALUES, COEFFS = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -37,6 +38,8 @@ _sig = {
                                             ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_bdf_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       ctypes.POINTER(ctypes.c_size_t)]),
+    'cyl_plan_item_tables': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            _c_double_p, _c_double_p]),
     'cyl_destroy': (ctypes.c_int, [_vp]),
     'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
     'cyl_coeffs2vals': (ctypes.c_int, [_vp, _vp, _vp]),
@@ -247,6 +250,17 @@ class Plan:
         qs = (ctypes.c_double * J.value)()
         _check(_lib.cyl_plan_shifts(self._h, which, k, parity, ctypes.byref(J), iv, ps, qs), 'cyl_plan_shifts')
         return J.value, tuple(iv), np.array(ps), np.array(qs)
+
+    def item_tables(self, which, item, j):
+        """(info dict, radial records, vertical records) of one item's ADI iteration j."""
+        info = (ctypes.c_int * 8)()
+        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, info, None, None), 'cyl_plan_item_tables')
+        M, Nz, J, twr, twz = info[0], info[1], info[2], info[3], info[4]
+        rad = (ctypes.c_double * (M * 12 + (24 if twr else 0)))()
+        ver = (ctypes.c_double * (Nz * 8 + (16 if twz else 0)))()
+        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, info, rad, ver), 'cyl_plan_item_tables')
+        keys = ('M', 'Nz', 'J', 'twr', 'twz', 'k', 'pr', 'pz')
+        return dict(zip(keys, list(info))), np.array(rad), np.array(ver)
 
     def operator(self, op, which, k, parity):
         """Dense parity block of A (op 0), C (1), B (2) or D (3)."""

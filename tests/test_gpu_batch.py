@@ -40,10 +40,13 @@ def _run_batch(bp, T0s, gs, steps):
     return [bp.view(T, i).cpu().numpy() for i in range(len(T0s))]
 
 
-def _run_plain(cyl, shapes, alpha, dt, T0s, gs, steps):
+def _run_plain(cyl, shapes, alpha, dt, T0s, gs, steps, twisted=False):
+    """Per-problem runs; plain LU sweeps unless twisted (the batch kernel's
+    arithmetic, so equal bit for bit)."""
     out = []
     for (p, m, n), a, x, gg in zip(shapes, alpha, T0s, gs):
-        pl = cyl.Plan(m, n, p, a, dt, 1e-14, poisson=False, heat=True)
+        pl = cyl.Plan(m, n, p, a, dt, 1e-14, poisson=False, heat=True,
+                      extra_flags=0 if twisted else cyl.PLAIN_SWEEPS)
         T = torch.as_tensor(x, device='cuda').clone()
         pl.heat_step(T, torch.as_tensor(gg, device='cuda'), steps)
         pl.sync()
@@ -65,6 +68,9 @@ def test_batch_equals_single_problem_runs_for_every_config(cyl):
         got = _run_batch(bp, T0s, gs, steps)
         for a, b in zip(got, plain):
             assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
+    # the per-problem plans' default (twisted sweeps on the small grids) agree to rounding
+    for a, b in zip(_run_plain(cyl, bp.shapes, alpha, dt, T0s, gs, steps, twisted=True), plain):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
 
 
 def test_batch_matches_oracle(cyl):

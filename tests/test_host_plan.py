@@ -190,3 +190,99 @@ def test_bdf_plan_builds_every_order_with_its_kappa(cyl):
         with pytest.raises(cyl.CylError) as ei:
             cyl.Plan(m, n, p, alpha, dt, 1e-13, poisson=False, heat=True, host_only=True, bdf_order=bad)
         assert ei.value.status == cyl.EINVAL
+
+
+def _radial_column(rec, R, U, f, first, k):
+    """One column of the radial sweep from the plan's records (the kernel's
+    arithmetic order is not reproduced, only its algebra)."""
+    M = len(f)
+    y = f.copy()
+    if not first:
+        for i in range(M):
+            for o in range(-2, 4):
+                if 0 <= i + o < M:
+                    y[i] += rec[i, o + 2] * U[i + o]
+    z = np.zeros(M + 3)
+    w = np.zeros(M)
+    top = M if k == 0 else k
+    for i in range(top):
+        w[i] = y[i] + (rec[i, 6] * w[i - 1] if i >= 1 else 0) + (rec[i, 7] * w[i - 2] if i >= 2 else 0)
+    if k:
+        v = np.zeros(M + 3)
+        for i in range(M - 1, k + 2, -1):
+            v[i] = y[i] + rec[i, 6] * v[i + 1] + rec[i, 7] * v[i + 2] + rec[i, 8] * v[i + 3]
+        rhs = np.array([w[k - 2], w[k - 1], y[k], y[k + 1], y[k + 2], v[k + 3], v[k + 4], v[k + 5]])
+        z[k:k + 3] = R.reshape(3, 8) @ rhs
+        for i in range(k + 3, M):
+            z[i] = rec[i, 11] * v[i] + rec[i, 9] * z[i - 1] + rec[i, 10] * z[i - 2]
+    for i in range(top - 1, -1, -1):
+        z[i] = rec[i, 11] * w[i] + rec[i, 8] * z[i + 1] + rec[i, 9] * z[i + 2] + rec[i, 10] * z[i + 3]
+    return z[:M]
+
+
+def _vertical_row(rec, R, zrow, k):
+    Nz = len(zrow)
+    x = np.zeros(Nz + 2)
+    w = np.zeros(Nz)
+    top = Nz if k == 0 else k
+    for c in range(top):
+        w[c] = zrow[c] + (rec[c, 0] * w[c - 1] if c >= 1 else 0)
+    if k:
+        v = np.zeros(Nz + 2)
+        for c in range(Nz - 1, k + 1, -1):
+            v[c] = zrow[c] + rec[c, 0] * v[c + 1] + rec[c, 1] * v[c + 2]
+        xi = R[:15].reshape(3, 5) @ np.array([w[k - 1], zrow[k], zrow[k + 1], v[k + 2], v[k + 3]])
+        x[k:k + 2] = xi[:2]
+        for c in range(k + 2, Nz):
+            x[c] = rec[c, 3] * v[c] + rec[c, 2] * x[c - 1]
+        assert abs(x[k + 2] - xi[2]) <= 1e-10 * max(1.0, np.abs(xi).max())
+    for c in range(top - 1, -1, -1):
+        x[c] = rec[c, 3] * w[c] + rec[c, 1] * x[c + 1] + rec[c, 2] * x[c + 2]
+    x = x[:Nz]
+    u = np.zeros(Nz)
+    for c in range(Nz):
+        for o in range(-1, 3):
+            if 0 <= c + o < Nz:
+                u[c] += rec[c, 5 + o] * x[c + o]
+    return x, u
+
+
+@pytest.mark.parametrize('which', [0, 1, 4])
+def test_item_tables_drive_adi_to_the_direct_solve(cyl, which):
+    """Algorithm 1 run from the plan's own factor records (plain LU sweeps and
+    the twisted two-sided sweeps with their interface maps) reaches the direct
+    solution of every item's block Sylvester equation."""
+    m, n, p = 40, 36, 8
+    plan = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=True, heat=True, host_only=True, bdf_order=4)
+    rng = np.random.default_rng(3 + which)
+    seen_twisted = False
+    nitems = 0
+    while True:
+        try:
+            info, _, _ = plan.item_tables(which, nitems, 0)
+        except cyl.CylError:
+            break
+        nitems += 1
+    assert nitems > 0
+    for item in range(0, nitems, 3):
+        info, _, _ = plan.item_tables(which, item, 0)
+        M, Nz, J, kr, kz = info['M'], info['Nz'], info['J'], info['twr'], info['twz']
+        seen_twisted |= bool(kr and kz)
+        A, C = plan.operator(0, which, info['k'], info['pr']), plan.operator(1, which, info['k'], info['pr'])
+        B, D = plan.operator(2, which, info['k'], info['pz']), plan.operator(3, which, info['k'], info['pz'])
+        ii, jj = np.meshgrid(np.arange(M), np.arange(Nz), indexing='ij')
+        E = rng.standard_normal((M, Nz)) * 1.3 ** (-(ii + jj))
+        U = np.zeros((M, Nz))
+        X = None
+        for j in range(J):
+            _, rad, ver = plan.item_tables(which, item, j)
+            rrec, Rr = rad[:M * 12].reshape(M, 12), rad[M * 12:]
+            vrec, Rz = ver[:Nz * 8].reshape(Nz, 8), ver[Nz * 8:]
+            Z = np.stack([_radial_column(rrec, Rr, U[:, c], E[:, c], j == 0, kr) for c in range(Nz)], axis=1)
+            rows = [_vertical_row(vrec, Rz, Z[a], kz) for a in range(M)]
+            X = np.stack([r[0] for r in rows])
+            U = np.stack([r[1] for r in rows])
+        Xd = sy.solve_kron(A, B, C, D, E)
+        assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max(), (item, kr, kz)
+    assert seen_twisted
+    plan.close()
