@@ -73,6 +73,8 @@ typedef enum {
  * where every sweep has at most 128 chains (grids up to about 130); the
  * results then match the persistent batch kernel bit for bit */
 #define CYL_PLAIN_SWEEPS 128u
+/* build the horizontal (disk) Poisson tables for cyl_disk_poisson */
+#define CYL_WITH_DISK    256u
 
 /* space selector of cyl_poisson */
 #define CYL_VALUES 0
@@ -91,7 +93,7 @@ typedef enum {
  *              the iteration count per mode is J = ceil(log(16 gamma) log(4/tol) / pi^2).
  *   flags      CYL_WITH_POISSON and/or CYL_WITH_HEAT, optionally
  *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL, CYL_WITH_BC,
- *              CYL_PLAIN_SWEEPS.
+ *              CYL_PLAIN_SWEEPS; CYL_WITH_DISK (alone or with the others).
  *   stream     cudaStream_t on which every device call of this plan runs
  *              (NULL = legacy default stream).  Ignored with CYL_HOST_ONLY.
  *
@@ -154,6 +156,20 @@ cyl_status cyl_coeffs2vals(cyl_plan_t plan, const double *coeffs, double *vals);
  * space.  f and u may alias.  Needs CYL_WITH_POISSON.
  */
 cyl_status cyl_poisson(cyl_plan_t plan, const double *f, const double *bc, double *u, int space);
+
+/*
+ * cyl_disk_poisson -- the horizontal Poisson solve -Delta_h u = f,
+ * Delta_h = lap - d_z^2 (Section 4, eq. ptpoisson: the toroidal and poloidal
+ * potentials of the poloidal-toroidal decomposition), "diagonalised in theta
+ * and z": z enters as a parameter, so every (half-complex slice,
+ * z-coefficient) column is one banded radial tau solve of the r^2-multiplied
+ * operator -L_k of eq. HelmholtzMatEqn with u = 0 at r = -1 and r = +1 (the
+ * boundary conditions are unstated; no condition in z, as Delta_h has no z
+ * derivative).  f and u: device arrays of N float64 in the given space
+ * (CYL_VALUES or CYL_COEFFS); they may alias.  One launch in coefficient
+ * space (plus the transforms in value space).  Needs CYL_WITH_DISK.
+ */
+cyl_status cyl_disk_poisson(cyl_plan_t plan, const double *f, double *u, int space);
 
 /*
  * cyl_heat_step -- advance (d_t - alpha lap) T = g by nsteps BDF1 steps

@@ -52,6 +52,8 @@ struct cyl_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *d_err = nullptr;         // device status word written by bounded waits
   double *d_apart = nullptr;    // per-item partial sums of the alpha gradient
+  Item *d_disk_items = nullptr;  // horizontal (disk) Poisson items (k, radial class), CYL_WITH_DISK
+  int ndisk = 0, disk_threads = 0;
   double *d_lift = nullptr;     // coefficients of the lifting W of the boundary data
   double *d_corr = nullptr;     // right-side correction of the lifted problem
   size_t N = 0;
@@ -95,6 +97,7 @@ void free_device(cyl_plan_s *P) {
   cudaFree(P->d_apart);
   cudaFree(P->d_lift);
   cudaFree(P->d_corr);
+  cudaFree(P->d_disk_items);
 }
 
 cyl_status from_cuda(cudaError_t e) {
@@ -338,9 +341,9 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   *plan = nullptr;
   if (n_r < 4 || n_z < 4 || n_theta < 2 || (n_theta & 1)) return CYL_EINVAL;
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
-  if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT))) return CYL_EINVAL;
+  if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_WITH_DISK))) return CYL_EINVAL;
   if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL |
-                          CYL_TEST_NO_TMA | CYL_WITH_BC | CYL_PLAIN_SWEEPS))
+                          CYL_TEST_NO_TMA | CYL_WITH_BC | CYL_PLAIN_SWEEPS | CYL_WITH_DISK))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if (bdf_order < 1 || bdf_order > cyl::kMaxBdf) return CYL_EINVAL;
@@ -414,6 +417,24 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_apart, std::max(1, P->nitems[1]) * sizeof(double));
+  if (e == cudaSuccess && (flags & CYL_WITH_DISK)) {
+    std::vector<Item> di;
+    const int hh = n_theta / 2;
+    for (int k = 0; k <= hh; ++k)
+      for (int pr = 0; pr < 2; ++pr) {
+        const long long off = h.disk_off[k * 2 + pr];
+        if (off < 0) continue;
+        Item it{};
+        it.k = k; it.pr = pr; it.M = h.Mc[pr]; it.Mfull = h.Mfull[pr];
+        it.m = n_r; it.n = n_z; it.roff = off; it.r2off = h.r2off[pr];
+        it.s0 = k == 0 ? 0 : (k == hh ? n_theta - 1 : 2 * k - 1);
+        it.nsl = (k == 0 || k == hh) ? 1 : 2;
+        di.push_back(it);
+      }
+    P->ndisk = (int)di.size();
+    P->disk_threads = std::min(256, std::max(32, (2 * n_z + 31) / 32 * 32));
+    e = upload(&P->d_disk_items, di.data(), di.size());
+  }
   if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_lift, P->N * sizeof(double));
   if (e == cudaSuccess && (flags & CYL_WITH_BC)) e = cudaMalloc((void **)&P->d_corr, P->N * sizeof(double));
   bool all_smem = true;
@@ -465,6 +486,22 @@ cyl_status cyl_poisson(cyl_plan_t P, const double *f, const double *bc, double *
   double *U = space == CYL_VALUES ? P->d_tmp[2] : u;
   if ((s = run_adi(P, 0, F, U, nullptr, 0.0, 0, 1, nullptr, 1, bc != nullptr)) != CYL_OK) return s;
   return space == CYL_VALUES ? coeffs2vals_impl(P, P->d_tmp[2], u) : CYL_OK;
+}
+
+cyl_status cyl_disk_poisson(cyl_plan_t P, const double *f, double *u, int space) {
+  if (!P || !f || !u || (space != CYL_VALUES && space != CYL_COEFFS)) return CYL_EINVAL;
+  if (P->host_only || P->is_batch || !P->d_disk_items) return CYL_ESTATE;
+  const int zero_other = (P->hp.flags & CYL_BOTH_PARITIES) ? 0 : 1;
+  const long long slice = (long long)P->hp.m * P->hp.n;
+  if (space == CYL_COEFFS)
+    return from_cuda(cyl::launch_disk_poisson(P->d_disk_items, P->ndisk, P->d_fac, f, u, P->hp.n, slice, zero_other,
+                                              P->disk_threads, P->st));
+  cyl_status s = vals2coeffs_impl(P, f, P->d_tmp[2]);
+  if (s != CYL_OK) return s;
+  cudaError_t e = cyl::launch_disk_poisson(P->d_disk_items, P->ndisk, P->d_fac, P->d_tmp[2], P->d_tmp[2], P->hp.n,
+                                           slice, zero_other, P->disk_threads, P->st);
+  if (e != cudaSuccess) return from_cuda(e);
+  return coeffs2vals_impl(P, P->d_tmp[2], u);
 }
 
 cyl_status cyl_heat_step(cyl_plan_t P, double *T, const double *g, long long g_step_stride, int nsteps,

@@ -1191,6 +1191,71 @@ cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *
   return cudaGetLastError();
 }
 
+// Horizontal (disk) Poisson, Section 4 eq. ptpoisson: one thread per
+// (slice, z-coefficient) column of an item (k, radial class); right side
+// R_2 f on the tau rows, LU solve with -L_k, recombination X = S_r Y, all in
+// one pass over the column (in place: f may alias u, the right side reads f
+// through a register window ahead of the writes).
+__global__ void disk_poisson_kernel(const Item *__restrict__ items, const double *__restrict__ fac,
+                                    const double *F, double *U, int n, long long slice, int zero_other) {
+  const Item it = items[blockIdx.x];
+  const int M = it.M, Mf = it.Mfull, W = it.nsl * n;
+  const double *H = fac + it.roff, *r2 = fac + it.r2off;
+  const size_t st = 2 * (size_t)n;
+  for (int cidx = threadIdx.x; cidx < W; cidx += blockDim.x) {
+    const int sl = cidx / n, j = cidx - sl * n;
+    const size_t base = (size_t)(it.s0 + sl) * slice + (size_t)it.pr * n + j;
+    const double *Fc = F + base;
+    double *Uc = U + base;
+    double f0 = 0.0, f1 = Fc[0];
+    double f2 = Mf > 1 ? Fc[st] : 0.0, f3 = Mf > 2 ? Fc[2 * st] : 0.0, f4 = Mf > 3 ? Fc[3 * st] : 0.0;
+    double w1 = 0.0, w2 = 0.0;
+    for (int a = 0; a < M; ++a) {
+      const double *rr = r2 + a * R2STRIDE;
+      const double *h = H + a * HSTRIDE;
+      double e = rr[0] * f0;
+      e = fma(rr[1], f1, e);
+      e = fma(rr[2], f2, e);
+      e = fma(rr[3], f3, e);
+      e = fma(rr[4], f4, e);
+      const double fnext = (a + 4 < Mf) ? Fc[(a + 4) * st] : 0.0;
+      const double w = fma(h[0], w1, fma(h[1], w2, e));
+      Uc[a * st] = w;
+      f0 = f1; f1 = f2; f2 = f3; f3 = f4; f4 = fnext;
+      w2 = w1;
+      w1 = w;
+    }
+    double y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int a = M - 1; a >= 0; --a) {
+      const double *h = H + a * HSTRIDE;
+      double y = h[5] * Uc[a * st];
+      y = fma(h[4], y3, y);
+      y = fma(h[3], y2, y);
+      y = fma(h[2], y1, y);
+      Uc[a * st] = y;
+      y3 = y2; y2 = y1; y1 = y;
+    }
+    // x_a = y_{a-1} - y_a (phi_a = T_{pr+2a+2} - T_{pr+2a}), top down so y_{a-1} is still intact
+    for (int a = Mf - 1; a >= 0; --a) {
+      const double ya = a < M ? Uc[a * st] : 0.0;
+      const double yb = a >= 1 ? Uc[(a - 1) * st] : 0.0;
+      Uc[a * st] = yb - ya;
+    }
+    if (zero_other) {
+      double *Uo = U + (size_t)(it.s0 + sl) * slice + (size_t)(1 - it.pr) * n + j;
+      const int Mo = (it.m - (1 - it.pr) + 1) / 2;
+      for (int a = 0; a < Mo; ++a) Uo[a * st] = 0.0;
+    }
+  }
+}
+
+cudaError_t launch_disk_poisson(const Item *items, int nitems, const double *fac, const double *F, double *U,
+                                int n, long long slice, int zero_other, int threads, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  disk_poisson_kernel<<<nitems, threads, 0, st>>>(items, fac, F, U, n, slice, zero_other);
+  return cudaGetLastError();
+}
+
 // Slot permutation of up to 5 N-element arrays: dst slot k = src slot
 // map.src[k] (a negative entry writes zeros).  Each thread owns one element
 // position of every slot and reads before it writes, so dst may equal src

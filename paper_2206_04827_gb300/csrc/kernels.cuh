@@ -75,6 +75,8 @@ cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, 
 cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
                         double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
                         int threads, cudaStream_t st);
+cudaError_t launch_disk_poisson(const Item *items, int nitems, const double *fac, const double *F, double *U,
+                                int n, long long slice, int zero_other, int threads, cudaStream_t st);
 constexpr int kMaxSlots = 5;
 struct SlotMap {
   int src[kMaxSlots];

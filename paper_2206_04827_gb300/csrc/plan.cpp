@@ -546,6 +546,27 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
       if (F.size() & 1) F.push_back(0.0);
     }
 
+  hp.r2off[0] = r2off[0];
+  hp.r2off[1] = r2off[1];
+  // horizontal (disk) Poisson: LU of -L_k per (k, class) (flag CYL_WITH_DISK)
+  hp.disk_off.assign((h + 1) * 2, -1);
+  if (flags & 256u) {
+    for (int k = 0; k <= h; ++k)
+      for (int pr = 0; pr < 2; ++pr) {
+        if (hp.Mc[pr] == 0 || (!both && pr != (k & 1))) continue;
+        Band A = axpby(-1.0, widen(hp.Lblk(k, pr), 2, 3), 0.0, Cb[pr]);
+        if (!lu_inplace(A)) return "disk LU failed (zero pivot)";
+        hp.disk_off[k * 2 + pr] = (long long)F.size();
+        const int M = hp.Mc[pr];
+        for (int i = 0; i < M; ++i) {
+          const double d = 1.0 / A.get(i, i);
+          F.push_back(i >= 1 ? -A.get(i, i - 1) : 0.0);
+          F.push_back(i >= 2 ? -A.get(i, i - 2) : 0.0);
+          for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -A.get(i, i + o) * d : 0.0);
+          F.push_back(d);
+        }
+      }
+  }
   // twisted solves only where both sweeps' chains (two slices x class size) fit kTwistMaxChains:
   // there the second half of the threads doubles the warps per SM sub-partition
   const bool tw_ok = twist && 2 * std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1])) <=

@@ -63,6 +63,10 @@ constexpr int RTWIST = 24;
 constexpr int ZTWIST = 16;
 constexpr int kTwistMinM = 10, kTwistMinN = 8;
 constexpr int kTwistMaxChains = 128;
+// Horizontal (disk) Poisson: LU records of -L_k (recombined, tau rows) per
+// class row: [0..1] -L[i][i-1], -L[i][i-2]; [2..4] -U[i][i+1..i+3]/U[i][i];
+// [5] 1/U[i][i].
+constexpr int HSTRIDE = 6;
 constexpr int R2STRIDE = 5;
 constexpr int C02STRIDE = 3;
 
@@ -118,6 +122,8 @@ struct HostPlan {
   std::vector<double> mu_min, mu_max;   // index k * 2 + pr
   double nu_min[2] = {0, 0}, nu_max[2] = {0, 0};
   int bdf_order = 1;                    // highest BDF order built (heat)
+  std::vector<long long> disk_off;      // per (k, pr): HSTRIDE records of -L_k, or -1
+  long long r2off[2] = {0, 0};          // R_2 band tables per radial class
   KindTables kind[kNumKinds];           // 0 = Poisson, 1..bdf_order = BDF 1..b
   std::vector<double> factors;          // all radial and vertical factor rows + rhs bands
   // transform matrices (row-major, out index major): forward and inverse

@@ -23,7 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # status codes and flags (include/cyl.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA, WITH_BC = 1, 2, 4, 8, 16, 32, 64
-PLAIN_SWEEPS = 128
+PLAIN_SWEEPS, WITH_DISK = 128, 256
 VALUES, COEFFS = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -40,6 +40,7 @@ _sig = {
                                                       ctypes.POINTER(ctypes.c_size_t)]),
     'cyl_plan_item_tables': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             _c_double_p, _c_double_p]),
+    'cyl_disk_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     'cyl_destroy': (ctypes.c_int, [_vp]),
     'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
     'cyl_coeffs2vals': (ctypes.c_int, [_vp, _vp, _vp]),
@@ -165,6 +166,12 @@ class Plan:
         nodes hold the Dirichlet data (include/cyl.h: cyl_poisson)."""
         _check(_lib.cyl_poisson(self._h, _ptr(f, 'f', self.N), _ptr(bc, 'bc', self.N), _ptr(u, 'u', self.N),
                                 int(space)), 'cyl_poisson')
+        return u
+
+    def disk_poisson(self, f, u, space=COEFFS):
+        """-Delta_h u = f, the horizontal (disk) Poisson solve (include/cyl.h: cyl_disk_poisson)."""
+        _check(_lib.cyl_disk_poisson(self._h, _ptr(f, 'f', self.N), _ptr(u, 'u', self.N), int(space)),
+               'cyl_disk_poisson')
         return u
 
     def heat_step(self, T, g=None, nsteps=1, g_step_stride=0, ckpt=None, ckpt_every=1, bc=None):
