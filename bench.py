@@ -15,6 +15,8 @@ Other workloads (same JSON line, for the other problem sizes of the method):
               per-problem form is timed beside the batched form
   adjoint128  128^3, alpha 0.5, dt 1e-3, 200 steps, checkpoint every 20:
               forward run + adjoint (gradients in T0, space-time g, alpha)
+  heat128_bdf4  the default problem under BDF 4 (100 steps from T0 alone: the
+              first three steps start up through BDF 1-3)
 
 Legs: --impl ours (default) times the CUDA path through the C ABI; --impl
 reference times the FP64 CPU oracle on the host cores on a bounded sample of
@@ -148,9 +150,12 @@ def adi_flops_per_launch(plan, nsteps):
 # ----------------------------------------------------------------- workloads
 class Workload:
     """units: unknowns*steps per bench step; flops: algorithmic FP64 flops of
-    the dominant kernel per bench step; launches: our kernel launches per step."""
+    the dominant kernel per bench step; launches: our kernel launches per step;
+    traffic: DRAM bytes (read + write) of one launch of the dominant kernel
+    from an ncu capture of this workload (profiles/), or None."""
     name = ''
     config = {}
+    traffic = None
 
     def reset(self):
         pass
@@ -161,6 +166,9 @@ class Workload:
 
 class Heat128(Workload):
     name = 'heat128'
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch
+    # (49,261,312 + 1,183,488 bytes; profiles/adi_kernel_heat128.md)
+    TRAFFIC = 49261312 + 1183488
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
         self.torch = torch
@@ -177,6 +185,7 @@ class Heat128(Workload):
         self.flops = self.plan.flops(1, nsteps)
         self.launches = 1
         self.kernel = 'adi_kernel'
+        self.traffic = self.TRAFFIC if nsteps == NSTEPS else None
         self.config = {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF1 steps, '
                                    '8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
                        'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nsteps, 'adi_tol': TOL}
@@ -410,8 +419,46 @@ class Adjoint128(Workload):
         return self.host[0].numel() * 8, self.host[1].numel() * 8
 
 
+class Heat128Bdf4(Heat128):
+    name = 'heat128_bdf4'
+    ORDER = 4
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        super().__init__(cyl, torch, dev, stream, nsteps)
+        b = self.ORDER
+        self.plan = cyl.Plan(M, N_Z, P, ALPHA, DT, TOL, poisson=False, heat=True, stream=stream.cuda_stream,
+                             bdf_order=b)
+        self.H = torch.zeros((b, P, M, N_Z), dtype=torch.float64, device=dev)
+        start = min(b - 1, nsteps)
+        self.flops = sum(self.plan.flops(o, 1) for o in range(1, start + 1)) + self.plan.flops(b, nsteps - start)
+        self.launches = start + (1 if nsteps > start else 0) + (1 if (-nsteps) % b else 0)
+        self.traffic = None
+        self.config = dict(self.config, workload='heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF4 steps '
+                           '(start-up through BDF 1-3), 8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
+                           bdf_order=b)
+
+    def reset(self):
+        self.H.zero_()
+        self.H[0].copy_(self.T0)
+
+    def step(self):
+        self.plan.heat_step_bdf(self.H, 1, self.g, self.nsteps)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.T0.cpu().pin_memory(), self.g.cpu().pin_memory(),
+                     t.empty(self.T0.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        T0h, gh, outh = self.host
+        self.H[0].copy_(T0h, non_blocking=True)
+        self.g.copy_(gh, non_blocking=True)
+        self.step()
+        outh.copy_(self.H[0], non_blocking=True)
+
+
 WORKLOADS = {'heat128': Heat128, 'poisson33': Poisson33, 'large512': Large512, 'batch256': Batch256,
-             'adjoint128': Adjoint128}
+             'adjoint128': Adjoint128, 'heat128_bdf4': Heat128Bdf4}
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -504,7 +551,7 @@ def run_ours(args):
         'config': dict(wl.config, l2='flushed between timed steps (256 MB write)',
                        parallelism='replicas' if world > 1 else 'single'),
         'roofline': {'bound': 'alu', 'achieved': achieved / 1e12, 'peak': peak / 1e12, 'unit': 'TFLOP/s',
-                     'frac': achieved / peak, 'traffic': None,
+                     'frac': achieved / peak, 'traffic': wl.traffic,
                      'peak_basis': '152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (of derived)',
                      'kernel': wl.kernel},
         'e2e': {'value': world * wl.units * len(e2e) / sum(e2e), 'unit': UNIT,
