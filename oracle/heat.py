@@ -46,6 +46,24 @@ class _systems(dict):
         return self[k]
 
 
+def _solve(ms, bs, E, brute, refine):
+    """Y with A Y B^T + C Y D^T = E: QZ Bartels-Stewart (or the dense Kronecker
+    solve when brute), then `refine` steps of iterative refinement whose
+    residual E - (A Y B^T + C Y D^T) is formed in extended precision
+    (np.longdouble).  Refinement is not part of the paper: a textbook remedy
+    for the forward error of the direct solve on large grids (about 1e-11 at
+    512 x 512 for the heat system), used to write stored reference values."""
+    Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+    if refine:
+        L = np.longdouble
+        A, B, C, D = (x.astype(L) for x in (ms.A, ms.B, ms.C, ms.D))
+        for _ in range(refine):
+            Yl = Y.astype(L)
+            R = E.astype(L) - (A @ Yl @ B.T + C @ Yl @ D.T)
+            Y = Y + bs.solve(np.asarray(R, dtype=np.float64))
+    return Y
+
+
 def lifting(bc_vals):
     """Coefficients of the transfinite (Gordon-Hall) blend of the boundary
     values of bc_vals ([p][m][n] grid values; only the nodes with j in
@@ -68,7 +86,7 @@ def lifting(bc_vals):
     return vals2coeffs(Pr + Pz - PrPz)
 
 
-def poisson(F, slices=None, brute=False, bc=None):
+def poisson(F, slices=None, brute=False, bc=None, refine=0):
     """Coefficients u of -lap u = f for half-complex coefficients F of f.
 
     bc: optional [p][m][n] grid values whose boundary nodes hold the Dirichlet
@@ -87,18 +105,19 @@ def poisson(F, slices=None, brute=False, bc=None):
             U[s] = bordered_solve(m, n, k, 'poisson', None, F[s], W[s])
             continue
         E = ms.rhs(F[s]) - ms.full_apply(W[s])
-        Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+        Y = _solve(ms, bs, E, brute, refine)
         U[s] = ms.expand(Y) + W[s]
     return U
 
 
-def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=False, bc=None):
+def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=False, bc=None, refine=0):
     """BDF1: X_{n+1} solves eq. HelmholtzMatEqn with delta X = X_n, kappa = dt.
 
     g is either one coefficient array (constant forcing) or an array of
     shape [nsteps][p][m][n] (g[n] is used by the step n -> n+1).  bc:
     optional time-constant Dirichlet data as in ``poisson`` (X_{n+1} = S Y S^T
-    + W, the right side corrected by the step operator applied to W)."""
+    + W, the right side corrected by the step operator applied to W).  refine:
+    steps of iterative refinement per solve (see ``_solve``)."""
     p, m, n = X0.shape
     kappa = dt
     sys_ = _systems(m, n, p, 'heat', kappa * alpha)
@@ -119,7 +138,7 @@ def heat_steps(X0, g, alpha, dt, nsteps, slices=None, brute=False, return_all=Fa
             E = ms.rhs(X[s] + kappa * gn[s])
             if W is not None:
                 E = E - ms.full_apply(W[s])
-            Y = solve_kron(ms.A, ms.B, ms.C, ms.D, E) if brute else bs.solve(E)
+            Y = _solve(ms, bs, E, brute, refine)
             Xn[s] = ms.expand(Y) + (W[s] if W is not None else 0.0)
         X = Xn
         if return_all:

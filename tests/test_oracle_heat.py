@@ -71,3 +71,26 @@ def test_large_step_reaches_poisson_steady_state():
     X = heat.heat_steps(np.zeros_like(G), G, alpha, 1e9, 1)
     U = heat.poisson(G / alpha)
     assert np.abs(X - U).max() < 1e-7 * np.abs(U).max()
+
+
+@pytest.mark.parametrize('m', [128, 256])
+def test_refinement_recovers_exact_polynomial_step_on_large_grids(m):
+    """One BDF1 step whose exact discrete solution is a known polynomial u
+    (tau-exact), on a large grid with a small kappa*alpha (the 512^3
+    workload's 1e-5): one step of iterative refinement with an extended
+    precision residual brings the direct solve to ~1e-14 (the plain QZ solve
+    drifts to ~1e-12 at m = 256)."""
+    alpha, h = 0.1, 1e-4
+    u = (1 - xs ** 2 - ys ** 2) * (1 - zs ** 2) * (xs * zs + ys ** 2 + 2)
+    v = (1 - xs ** 2 - ys ** 2) * (1 - zs ** 2) * (1 + xs * ys)
+    lap = sp.diff(u, xs, 2) + sp.diff(u, ys, 2) + sp.diff(u, zs, 2)
+    g = (u - h * alpha * lap - v) / h
+    p = 6
+    U, V, G = (tr.vals2coeffs(_on_grid(sp.lambdify((xs, ys, zs), e, 'numpy'), p, m, m)) for e in (u, v, g))
+    sl = [0, 1, 2]
+    X0 = heat.heat_steps(V, G, alpha, h, 1, slices=sl)
+    X1 = heat.heat_steps(V, G, alpha, h, 1, slices=sl, refine=1)
+    scale = np.abs(U).max()
+    e0 = np.abs(X0[sl] - U[sl]).max() / scale
+    e1 = np.abs(X1[sl] - U[sl]).max() / scale
+    assert e1 < 3e-14 and e1 <= e0
