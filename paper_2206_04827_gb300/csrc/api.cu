@@ -193,7 +193,8 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
   return from_cuda(cyl::launch_adi(a, P->threads[kind], P->smem[kind], P->st));
 }
 
-constexpr int kBatchThreads = 128;
+constexpr int kBatchThreads = 128;      // smallest CTA of the persistent batch kernel
+constexpr int kBatchMaxThreads = 512;
 
 // Split a batch's items into two launch classes (threshold on max(M, Nz)) and
 // build their device tables and work areas.  Pairs of Re/Im slices whose
@@ -224,7 +225,7 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
       const long long bands = 2LL * (cM * cyl::RSTRIDE + cNz * cyl::ZSTRIDE);
       const long long ldmax = ((long long)budget - bands) / cRows;
       if (ldmax < (cW1 | 1)) return CYL_EINVAL;
-      const int chains_max = 4 * (kBatchThreads / C.G);
+      const int chains_max = 4 * (kBatchMaxThreads / C.G);
       for (const Item &it0 : cand) {
         const bool pair_ok = it0.nsl == 2 && ((2 * it0.Nzfull) | 1) <= ldmax &&
                              2 * std::max(it0.M, it0.Nz) <= chains_max;
@@ -251,7 +252,12 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
       C.ld = std::max(C.ld, it.nsl * it.Nzfull);
     }
     C.ld |= 1;
-    C.threads = kBatchThreads;
+    // one thread per chain of the widest item (two warps per SM sub-partition for the
+    // large items, whose shared memory admits one CTA per SM), at most 512 per CTA
+    int chains = 32;
+    for (const Item &it : items) chains = std::max(chains, it.nsl * std::max(it.M, it.Nz));
+    const int per_group = std::min(kBatchMaxThreads / C.G, (chains + 31) / 32 * 32);
+    C.threads = std::max(kBatchThreads, C.G * per_group);
     C.smem = cyl::batch_smem_bytes(C.G, C.ld, C.smem_rows, C.maxM, C.maxNz);
     if (C.smem > kSmemLimit) return CYL_EINVAL;
     C.blocks = std::min(C.nitems, sms * std::max(1, (int)(kSmemLimit / std::max<size_t>(C.smem, 1))));

@@ -677,7 +677,10 @@ __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs 
 // UNR: unroll factor of the sweeps.  Measured on GB300: 2 with the work
 // arrays in shared memory; 8 with them in global memory, where more rows in
 // flight hide the load latency (1 is 6x slower there, 8 beats 4 by 15 %).
-template <bool TRANS, int UNR>
+// TW: compiled with the twisted sweeps (items whose tables carry twisted
+// solves, twr / twz > 0); without it only the one-sided sweeps are compiled,
+// which keeps the register allocation of the plain kernels unchanged.
+template <bool TRANS, int UNR, bool TW = false>
 __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &sh, const AdiArgs &a, const Item &it,
                                                double *S, const double *Fa, int ldF, long long &c, long long c0,
                                                long long c_end, bool &timed_out) {
@@ -694,7 +697,7 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const int xh = sh.xhalf;
     const bool bottom = gp.tid >= xh;
     const int chain = gp.tid - (bottom ? xh : 0);
-    if (!TRANS && it.twr) {
+    if (TW && !TRANS && it.twr) {
       if (chain < W) {
         if (jt == 0) radial_tw1<true, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
         else radial_tw1<false, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
@@ -708,7 +711,7 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
       }
     }
     gp.sync();
-    if (!TRANS && it.twz) {
+    if (TW && !TRANS && it.twz) {
       const int sl = chain / M, aa = chain - sl * M;
       double *rowp = S + aa * ld + sl * Nz;
       if (chain < nsl * M) vertical_tw1<UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
@@ -739,7 +742,7 @@ __device__ __forceinline__ void init_bars(const Grp &gp, unsigned long long *bar
 }
 
 // Every BDF1 step of one item (see adi_kernel): right side, ADI, expansion.
-template <int UNR>
+template <int UNR, bool TW = false>
 __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArgs &a, const Item &it,
                                                      const AdiShared &sh, double *S, double *Fa, long long &c,
                                                      bool &timed_out) {
@@ -813,7 +816,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     gp.sync();
 
-    adi_iterations<false, UNR>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
+    adi_iterations<false, UNR, TW>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
     const int Wf = nsl * it.Nzfull;
@@ -853,7 +856,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
 
 // One CTA per item.  S_SMEM / F_SMEM place the item's iterate (S) and right
 // side (Fa) in shared memory, else in the per-item global work area.
-template <bool S_SMEM, bool F_SMEM, int MAXT>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
 __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -876,7 +879,7 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   init_bars(gp, bar);
   bool timed_out = false;
   long long c = 0;
-  process_item_forward<S_SMEM ? 2 : 8>(gp, a, it, sh, S, Fa, c, timed_out);
+  process_item_forward<S_SMEM ? 2 : 8, TW>(gp, a, it, sh, S, Fa, c, timed_out);
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
 
@@ -1307,31 +1310,33 @@ cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, 
   return cudaGetLastError();
 }
 
-template <bool S_SMEM, bool F_SMEM, int MAXT>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
 static cudaError_t launch_adi_t(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(adi_kernel<S_SMEM, F_SMEM, MAXT>,
+  cudaError_t e = cudaFuncSetAttribute(adi_kernel<S_SMEM, F_SMEM, MAXT, TW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adi_kernel<S_SMEM, F_SMEM, MAXT><<<a.nitems, threads, smem, st>>>(a);
+  adi_kernel<S_SMEM, F_SMEM, MAXT, TW><<<a.nitems, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-// Blocks of at most 128 and 256 threads (plain and twisted sweeps of grids up
-// to about 130) get instantiations with a register budget of 255 per thread.
+template <bool S_SMEM, bool F_SMEM>
+static cudaError_t launch_adi_level(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
+  if (a.twist_half > 0)     // twisted plans use at most 2 x 128 threads
+    return threads <= 128 ? launch_adi_t<S_SMEM, F_SMEM, 128, true>(a, threads, smem, st)
+                          : launch_adi_t<S_SMEM, F_SMEM, 256, true>(a, threads, smem, st);
+  return threads <= 128   ? launch_adi_t<S_SMEM, F_SMEM, 128, false>(a, threads, smem, st)
+         : threads <= 256 ? launch_adi_t<S_SMEM, F_SMEM, 256, false>(a, threads, smem, st)
+                          : launch_adi_t<S_SMEM, F_SMEM, 512, false>(a, threads, smem, st);
+}
+
+// Blocks of at most 128 and 256 threads get instantiations with a register
+// budget of 255 per thread; the twisted sweeps get instantiations of their own.
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
-  const int t = threads <= 128 ? 128 : (threads <= 256 ? 256 : 512);
-  if (a.use_smem == 2)
-    return t == 128 ? launch_adi_t<true, true, 128>(a, threads, smem, st)
-           : t == 256 ? launch_adi_t<true, true, 256>(a, threads, smem, st)
-                      : launch_adi_t<true, true, 512>(a, threads, smem, st);
-  if (a.use_smem == 1)
-    return t == 128 ? launch_adi_t<true, false, 128>(a, threads, smem, st)
-           : t == 256 ? launch_adi_t<true, false, 256>(a, threads, smem, st)
-                      : launch_adi_t<true, false, 512>(a, threads, smem, st);
-  return t == 128 ? launch_adi_t<false, false, 128>(a, threads, smem, st)
-         : t == 256 ? launch_adi_t<false, false, 256>(a, threads, smem, st)
-                    : launch_adi_t<false, false, 512>(a, threads, smem, st);
+  if (a.twist_half > 0 && threads > 256) return cudaErrorInvalidValue;
+  if (a.use_smem == 2) return launch_adi_level<true, true>(a, threads, smem, st);
+  if (a.use_smem == 1) return launch_adi_level<true, false>(a, threads, smem, st);
+  return launch_adi_level<false, false>(a, threads, smem, st);
 }
 
 __global__ void axis_matvec_kernel(const double *__restrict__ in, double *__restrict__ out,
