@@ -298,7 +298,11 @@ cyl_status cyl_heat_adjoint_workspace(cyl_plan_t plan, int nsteps, int ckpt_ever
  * cyl_plan_batch -- one plan for nprob independent heat problems on grids
  * n_r[i] x n_z[i] x n_theta[i] (each 4 <= n_r, n_z <= 256, n_theta even >= 2),
  * diffusivities alpha[i] > 0, one step dt > 0 and one ADI tolerance.  flags:
- * CYL_WITH_HEAT (required), optionally CYL_BOTH_PARITIES.  The per-problem
+ * CYL_WITH_HEAT (required), optionally CYL_BOTH_PARITIES, CYL_PLAIN_SWEEPS
+ * (one-sided sweeps only; otherwise items of at most 128 chains per slice use
+ * twisted solves, two threads per chain), CYL_HOST_ONLY (host tables and the
+ * batch configuration only: cyl_batch_set_config / get_config work, the
+ * device calls return CYL_ESTATE).  The per-problem
  * host plans are built in parallel threads.  The batch arrays are the
  * problems' [p][m][n] coefficient arrays concatenated in problem order
  * (offsets from cyl_batch_layout).  Every (problem, wavenumber, parity) work

@@ -42,6 +42,7 @@ struct cyl_plan_s {
   struct BatchClass {
     Item *d_items = nullptr;
     int nitems = 0, G = 1, threads = 128, blocks = 0, ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
+    int twist_half = 0;
     size_t smem = 0;
     long long gwork_per_item = 0;
     double *d_gwork = nullptr;
@@ -76,9 +77,11 @@ cudaError_t upload(T **dst, const T *src, size_t count) {
 
 void free_batch(cyl_plan_s *P) {
   for (auto &c : P->bc) {
-    cudaFree(c.d_items);
-    cudaFree(c.d_gwork);
-    cudaFree(c.d_queue);
+    if (!P->host_only) {
+      cudaFree(c.d_items);
+      cudaFree(c.d_gwork);
+      cudaFree(c.d_queue);
+    }
     c = cyl_plan_s::BatchClass();
   }
 }
@@ -195,6 +198,7 @@ cyl_status run_adi(cyl_plan_s *P, int kind, const double *Xin, double *Xout, con
 
 constexpr int kBatchThreads = 128;      // smallest CTA of the persistent batch kernel
 constexpr int kBatchMaxThreads = 512;
+constexpr int kBatchDefaults[][2] = {{63, 4}, {63, 2}, {47, 4}, {31, 4}, {95, 2}, {0, 1}};   // (threshold, groups)
 
 // Split a batch's items into two launch classes (threshold on max(M, Nz)) and
 // build their device tables and work areas.  Pairs of Re/Im slices whose
@@ -203,7 +207,7 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
   free_batch(P);
   P->threshold = threshold;
   int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (!P->host_only) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   for (int cls = 0; cls < 2; ++cls) {
     auto &C = P->bc[cls];
     C.G = cls == 0 ? 1 : G_small;
@@ -222,13 +226,19 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
     std::vector<Item> items;
     if (!cand.empty()) {
       // widest row the group's slice can hold next to the double-buffered tables
+      bool ctw = false;
+      for (const Item &it0 : cand) ctw = ctw || it0.twr || it0.twz;
       const long long bands = 2LL * (cM * cyl::RSTRIDE + cNz * cyl::ZSTRIDE);
-      const long long ldmax = ((long long)budget - bands) / cRows;
+      const int tw_cap = std::min(cyl::kTwistMaxChains, kBatchMaxThreads / C.G / 2);
+      const long long extra =                    // interface maps and exchange scratch of twisted groups
+          ctw ? 2LL * (cyl::RTWIST + cyl::ZTWIST) + (long long)cyl::TW_SLOTS * tw_cap : 0;
+      const long long ldmax = ((long long)budget - bands - extra) / cRows;
       if (ldmax < (cW1 | 1)) return CYL_EINVAL;
-      const int chains_max = 4 * (kBatchMaxThreads / C.G);
+      const int chains_max = 4 * (kBatchMaxThreads / C.G);   // a twisted item: two threads per chain
       for (const Item &it0 : cand) {
+        const bool tw = it0.twr || it0.twz;
         const bool pair_ok = it0.nsl == 2 && ((2 * it0.Nzfull) | 1) <= ldmax &&
-                             2 * std::max(it0.M, it0.Nz) <= chains_max;
+                             2 * std::max(it0.M, it0.Nz) <= (tw ? tw_cap : chains_max);
         if (it0.nsl == 2 && !pair_ok) {
           Item a1 = it0, a2 = it0;
           a1.nsl = a2.nsl = 1;
@@ -255,14 +265,22 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
     // one thread per chain of the widest item (two warps per SM sub-partition for the
     // large items, whose shared memory admits one CTA per SM), at most 512 per CTA
     int chains = 32;
-    for (const Item &it : items) chains = std::max(chains, it.nsl * std::max(it.M, it.Nz));
-    const int per_group = std::min(kBatchMaxThreads / C.G, (chains + 31) / 32 * 32);
+    bool tw = false;
+    for (const Item &it : items) {
+      chains = std::max(chains, it.nsl * std::max(it.M, it.Nz));
+      tw = tw || it.twr || it.twz;
+    }
+    const int half = (chains + 31) / 32 * 32;
+    if (tw && (half > cyl::kTwistMaxChains || 2 * half * C.G > kBatchMaxThreads)) return CYL_EINVAL;
+    C.twist_half = tw ? half : 0;            // twisted groups: top chains, then bottom chains
+    const int per_group = tw ? 2 * half : std::min(kBatchMaxThreads / C.G, half);
     C.threads = std::max(kBatchThreads, C.G * per_group);
-    C.smem = cyl::batch_smem_bytes(C.G, C.ld, C.smem_rows, C.maxM, C.maxNz);
+    C.smem = cyl::batch_smem_bytes(C.G, C.ld, C.smem_rows, C.maxM, C.maxNz, C.twist_half);
     if (C.smem > kSmemLimit) return CYL_EINVAL;
     C.blocks = std::min(C.nitems, sms * std::max(1, (int)(kSmemLimit / std::max<size_t>(C.smem, 1))));
     C.blocks = std::max(1, std::min(C.blocks, 4 * sms));
     C.gwork_per_item = ((long long)C.maxM * C.ld + 31) / 32 * 32;
+    if (P->host_only) continue;              // configuration only (host-side checks)
     cudaError_t e = upload(&C.d_items, items.data(), items.size());
     if (e == cudaSuccess)
       e = cudaMalloc((void **)&C.d_gwork, (size_t)C.gwork_per_item * C.blocks * C.G * sizeof(double));
@@ -304,7 +322,8 @@ cyl_status run_batch(cyl_plan_s *P, double *T, const double *g, int nsteps) {
     a.maxNz = C.maxNz;
     a.err = P->d_err;
     a.wait_limit = kWaitCycles;
-    a.group_doubles = (long long)cyl::batch_group_doubles(C.ld, C.smem_rows, C.maxM, C.maxNz);
+    a.group_doubles = (long long)cyl::batch_group_doubles(C.ld, C.smem_rows, C.maxM, C.maxNz, C.twist_half);
+    a.twist_half = C.twist_half;
     if (a.group_doubles % 32 != 0 || (size_t)a.group_doubles * C.G * sizeof(double) > C.smem) return CYL_EINVAL;
     cudaStream_t st = (two && cls == 1) ? P->aux : P->st;
     e = cyl::launch_batch(a, C.d_queue, C.G, C.threads, C.blocks, C.smem, st);
@@ -936,7 +955,9 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
   *plan = nullptr;
   if (nprob < 1 || !n_r || !n_z || !n_theta || !alpha || !(dt > 0.0)) return CYL_EINVAL;
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
-  if (!(flags & CYL_WITH_HEAT) || (flags & ~(unsigned)(CYL_WITH_HEAT | CYL_BOTH_PARITIES))) return CYL_EINVAL;
+  if (!(flags & CYL_WITH_HEAT) ||
+      (flags & ~(unsigned)(CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_PLAIN_SWEEPS | CYL_HOST_ONLY)))
+    return CYL_EINVAL;
   for (int i = 0; i < nprob; ++i)
     if (n_r[i] < 4 || n_z[i] < 4 || n_theta[i] < 2 || (n_theta[i] & 1) || !(alpha[i] > 0.0) ||
         n_r[i] > 256 || n_z[i] > 256)
@@ -955,9 +976,10 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
     pool.emplace_back([&, t]() {
       for (int i = t; i < nprob; i += nth) {
         try {
-          // the persistent batch kernel runs plain (untwisted) sweeps
+          // twisted solves per single slice (configure_batch splits twisted pairs)
           errs[i] = cyl::build_host_plan(hps[i], n_r[i], n_z[i], n_theta[i], alpha[i], dt, adi_tol,
-                                         (flags & CYL_BOTH_PARITIES) | CYL_WITH_HEAT, 1, false);
+                                         (flags & CYL_BOTH_PARITIES) | CYL_WITH_HEAT, 1,
+                                         (flags & CYL_PLAIN_SWEEPS) ? 0 : 2);
         } catch (...) {
           errs[i] = "host plan failed";
         }
@@ -995,6 +1017,18 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
   P->hp.dt = dt;
   P->hp.tol = adi_tol;
   P->hp.kind[1].built = true;
+  P->host_only = (flags & CYL_HOST_ONLY) != 0;
+  if (P->host_only) {                        // host tables and the batch configuration only
+    cyl_status s = CYL_EINVAL;
+    for (const auto &d : kBatchDefaults)
+      if ((s = configure_batch(P, d[0], d[1])) == CYL_OK) break;
+    if (s != CYL_OK) {
+      delete P;
+      return s;
+    }
+    *plan = P;
+    return CYL_OK;
+  }
   cudaError_t e = cudaGetDevice(&P->device);
   if (e == cudaSuccess) e = upload(&P->d_fac, fac.data(), fac.size());
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
@@ -1003,7 +1037,9 @@ cyl_status cyl_plan_batch(cyl_plan_t *plan, int nprob, const int *n_r, const int
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
   cyl_status s = from_cuda(e);
-  if (s == CYL_OK) s = configure_batch(P, 63, 4);
+  if (s == CYL_OK)                           // first feasible default (the autotuner refines it)
+    for (const auto &d : kBatchDefaults)
+      if ((s = configure_batch(P, d[0], d[1])) == CYL_OK) break;
   if (s != CYL_OK) {
     free_device(P);
     delete P;
@@ -1023,7 +1059,7 @@ cyl_status cyl_batch_layout(cyl_plan_t P, int *nprob, long long *offsets) {
 
 cyl_status cyl_heat_step_batch(cyl_plan_t P, double *T, const double *g, int nsteps) {
   if (!P || !T || nsteps < 0) return CYL_EINVAL;
-  if (!P->is_batch) return CYL_ESTATE;
+  if (!P->is_batch || P->host_only) return CYL_ESTATE;
   if (nsteps == 0) return CYL_OK;
   return run_batch(P, T, g, nsteps);
 }
@@ -1046,6 +1082,7 @@ cyl_status cyl_batch_get_config(cyl_plan_t P, int *threshold, int *groups, int *
 
 cyl_status cyl_batch_autotune(cyl_plan_t P, const double *T, const double *g, int nsteps, double *best_ms) {
   if (!P || !P->is_batch || !T || nsteps < 1) return CYL_EINVAL;
+  if (P->host_only) return CYL_ESTATE;
   double *work = nullptr;
   cudaError_t e = cudaMalloc((void **)&work, P->N * sizeof(double));
   if (e != cudaSuccess) return from_cuda(e);

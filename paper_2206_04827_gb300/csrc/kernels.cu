@@ -887,8 +887,8 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
 // threads; each group pulls items (largest first) from a queue and runs every
 // step of each.  S lives in the group's shared-memory slice, Fa in the
 // group's global work area.
-template <int G>
-__global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int *queue) {
+template <int G, bool TW, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) adi_batch_kernel(const AdiArgs a, int *queue) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2 * G];
   __shared__ int next_item[G];
@@ -898,14 +898,14 @@ __global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int 
   // double2 loads of the factor tables need 16-byte alignment)
   double *base = sm + (size_t)g * (size_t)a.group_doubles;
   AdiShared sh;
-  sh.rlen = a.maxM * RSTRIDE;
-  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.rlen = a.maxM * RSTRIDE + (TW ? RTWIST : 0);
+  sh.zlen = a.maxNz * ZSTRIDE + (TW ? ZTWIST : 0);
   sh.RB0 = base;
   sh.ZB0 = base + 2 * sh.rlen;
   sh.bar = bar + 2 * g;
-  sh.xs = nullptr;        // batch items are never twisted
-  sh.xhalf = gsize;
   double *S = sh.ZB0 + 2 * sh.zlen;
+  sh.xs = TW ? S + (size_t)a.smem_rows * a.ld : nullptr;   // twisted-sweep exchange, after S
+  sh.xhalf = TW ? a.twist_half : gsize;
   double *Fa = a.gwork + ((size_t)blockIdx.x * G + g) * a.gwork_per_item;
   init_bars(gp, sh.bar);
   bool timed_out = false;
@@ -917,18 +917,41 @@ __global__ void __launch_bounds__(512, 1) adi_batch_kernel(const AdiArgs a, int 
     gp.sync();
     if (idx >= a.nitems) break;
     const Item it = a.items[idx];
-    process_item_forward<2>(gp, a, it, sh, S, Fa, c, timed_out);
+    process_item_forward<2, TW>(gp, a, it, sh, S, Fa, c, timed_out);
   }
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
 
-size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz) {
-  const size_t d = (size_t)2 * (maxM * RSTRIDE + maxNz * ZSTRIDE) + (size_t)smem_rows * ld;
+// One group's shared-memory slice: double-buffered tables, S, and (twisted
+// groups) the interface maps and the exchange scratch; a multiple of 32
+// doubles so every group's slice starts 256-byte aligned.
+size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz, int twist_half) {
+  const size_t tails = twist_half ? (size_t)(RTWIST + ZTWIST) : 0;
+  const size_t d = (size_t)2 * (maxM * RSTRIDE + maxNz * ZSTRIDE + tails) + (size_t)smem_rows * ld +
+                   (size_t)TW_SLOTS * twist_half;
   return (d + 31) / 32 * 32;
 }
 
-size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz) {
-  return batch_group_doubles(ld, smem_rows, maxM, maxNz) * G * sizeof(double);
+size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz, int twist_half) {
+  return batch_group_doubles(ld, smem_rows, maxM, maxNz, twist_half) * G * sizeof(double);
+}
+
+template <int G, bool TW>
+static cudaError_t launch_batch_t(const AdiArgs &a, int *queue, int threads, int blocks, size_t smem,
+                                  cudaStream_t st) {
+  // CTAs of at most 256 threads get the full register budget (no spills in the sweeps)
+  if (threads <= 256) {
+    cudaError_t e = cudaFuncSetAttribute(adi_batch_kernel<G, TW, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_batch_kernel<G, TW, 256><<<blocks, threads, smem, st>>>(a, queue);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(adi_batch_kernel<G, TW, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    adi_batch_kernel<G, TW, 512><<<blocks, threads, smem, st>>>(a, queue);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int blocks, size_t smem,
@@ -936,24 +959,16 @@ cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int b
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  const bool tw = a.twist_half > 0;
   switch (G) {
-    case 1:
-      e = cudaFuncSetAttribute(adi_batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) adi_batch_kernel<1><<<blocks, threads, smem, st>>>(a, queue);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(adi_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) adi_batch_kernel<2><<<blocks, threads, smem, st>>>(a, queue);
-      break;
-    case 4:
-      e = cudaFuncSetAttribute(adi_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) adi_batch_kernel<4><<<blocks, threads, smem, st>>>(a, queue);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 1: return tw ? launch_batch_t<1, true>(a, queue, threads, blocks, smem, st)
+                      : launch_batch_t<1, false>(a, queue, threads, blocks, smem, st);
+    case 2: return tw ? launch_batch_t<2, true>(a, queue, threads, blocks, smem, st)
+                      : launch_batch_t<2, false>(a, queue, threads, blocks, smem, st);
+    case 4: return tw ? launch_batch_t<4, true>(a, queue, threads, blocks, smem, st)
+                      : launch_batch_t<4, false>(a, queue, threads, blocks, smem, st);
+    default: return cudaErrorInvalidValue;
   }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
 }
 
 // Adjoint of the BDF1 steps n = n_hi-1 .. n_lo for one item (the transpose of

@@ -87,8 +87,8 @@ cudaError_t launch_sum_partials(const double *part, int n, double scale, double 
 
 constexpr int TW_SLOTS = 11;   // exchange doubles per chain of a twisted sweep
 size_t adi_smem_bytes(int ld, int smem_rows, int maxM, int maxNz, int level, int twist_half);
-size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz);
-size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz);
+size_t batch_group_doubles(int ld, int smem_rows, int maxM, int maxNz, int twist_half);
+size_t batch_smem_bytes(int G, int ld, int smem_rows, int maxM, int maxNz, int twist_half);
 cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int blocks, size_t smem,
                          cudaStream_t st);
 

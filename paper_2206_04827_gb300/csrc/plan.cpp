@@ -457,7 +457,7 @@ void bdf_beta(int b, double beta[kMaxBdf]) {
 }
 
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags, int bdf_order, bool twist) {
+                            unsigned flags, int bdf_order, int twist) {
   if (bdf_order < 1 || bdf_order > kMaxBdf) return "BDF order out of range";
   hp.m = m; hp.n = n; hp.p = p; hp.alpha = alpha; hp.dt = dt; hp.tol = tol; hp.flags = flags;
   hp.bdf_order = bdf_order;
@@ -569,8 +569,8 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
   }
   // twisted solves only where both sweeps' chains (two slices x class size) fit kTwistMaxChains:
   // there the second half of the threads doubles the warps per SM sub-partition
-  const bool tw_ok = twist && 2 * std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1])) <=
-                                  kTwistMaxChains;
+  const int maxclass = std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1]));
+  const bool tw_ok = (twist == 1 && 2 * maxclass <= kTwistMaxChains) || (twist == 2 && maxclass <= kTwistMaxChains);
   for (int kind = 0; kind < kNumKinds; ++kind) {
     KindTables &KT = hp.kind[kind];
     KT = KindTables();

@@ -137,10 +137,11 @@ struct HostPlan {
 };
 
 // Build everything on the host.  Returns an empty string on success, else a message.
-// twist: allow twisted (two-sided) solves where both sweeps' chain counts fit
-// 128 threads (see kTwistMaxChains); batch plans pass false.
+// twist: 0 = one-sided sweeps only; 1 = twisted (two-sided) solves where both
+// sweeps of a two-slice item have at most kTwistMaxChains chains; 2 = where
+// one slice has (batch plans, which split twisted pairs into single slices).
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
-                            unsigned flags, int bdf_order = 1, bool twist = true);
+                            unsigned flags, int bdf_order = 1, int twist = 1);
 
 double ellip_K(double kprime);
 double jacobi_dn(double u, double kprime);

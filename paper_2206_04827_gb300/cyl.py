@@ -281,16 +281,19 @@ class Plan:
 class BatchPlan:
     """Owner of a batch plan (see include/cyl.h: cyl_plan_batch)."""
 
-    def __init__(self, n_r, n_z, n_theta, alpha, dt, adi_tol=1e-14, both_parities=False, stream=None):
+    def __init__(self, n_r, n_z, n_theta, alpha, dt, adi_tol=1e-14, both_parities=False, stream=None,
+                 plain_sweeps=False, host_only=False):
         k = len(n_r)
-        if stream is None:
+        if stream is None and not host_only:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         ia = lambda v: (ctypes.c_int * k)(*[int(x) for x in v])
         self._h = _vp()
         _check(_lib.cyl_plan_batch(ctypes.byref(self._h), k, ia(n_r), ia(n_z), ia(n_theta),
                                    (ctypes.c_double * k)(*[float(a) for a in alpha]), float(dt), float(adi_tol),
-                                   WITH_HEAT | (BOTH_PARITIES if both_parities else 0), _vp(stream)),
+                                   WITH_HEAT | (BOTH_PARITIES if both_parities else 0)
+                                   | (PLAIN_SWEEPS if plain_sweeps else 0) | (HOST_ONLY if host_only else 0),
+                                   _vp(stream) if stream else None),
                'cyl_plan_batch')
         offs = (ctypes.c_longlong * (k + 1))()
         _check(_lib.cyl_batch_layout(self._h, None, offs), 'cyl_batch_layout')

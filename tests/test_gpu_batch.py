@@ -59,16 +59,26 @@ def test_batch_equals_single_problem_runs_for_every_config(cyl):
     rng = np.random.default_rng(31)
     n_r, n_z, n_t, alpha = _batch(rng, 7, 6, 72, [4, 8, 16])
     dt, steps = 1e-3, 4
-    bp = cyl.BatchPlan(n_r, n_z, n_t, alpha, dt, 1e-14)
+    bp = cyl.BatchPlan(n_r, n_z, n_t, alpha, dt, 1e-14, plain_sweeps=True)
     T0s = _fields(rng, bp.shapes)
     gs = _fields(rng, bp.shapes)
     plain = _run_plain(cyl, bp.shapes, alpha, dt, T0s, gs, steps)
-    for thr, G in [(63, 4), (0, 1), (31, 2), (15, 4), (95, 1), (47, 2)]:
+    configs = [(63, 4), (0, 1), (31, 2), (15, 4), (95, 1), (47, 2)]
+    # one-sided sweeps in both forms: the same arithmetic, bit for bit
+    for thr, G in configs:
         bp.set_config(thr, G)
         got = _run_batch(bp, T0s, gs, steps)
         for a, b in zip(got, plain):
             assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
-    # the per-problem plans' default (twisted sweeps on the small grids) agree to rounding
+    # the default batch (twisted solves per slice) and the per-problem default agree to rounding
+    tw = cyl.BatchPlan(n_r, n_z, n_t, alpha, dt, 1e-14)
+    for thr, G in configs:
+        try:
+            tw.set_config(thr, G)
+        except cyl.CylError:
+            continue          # a twisted class may not fit this (threshold, groups) setting
+        for a, b in zip(_run_batch(tw, T0s, gs, steps), plain):
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
     for a, b in zip(_run_plain(cyl, bp.shapes, alpha, dt, T0s, gs, steps, twisted=True), plain):
         assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
 

@@ -286,3 +286,38 @@ def test_item_tables_drive_adi_to_the_direct_solve(cyl, which):
         assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max(), (item, kr, kz)
     assert seen_twisted
     plan.close()
+
+
+def test_batch_configuration_on_host(cyl):
+    """Host-only batch plan of uneven grids: a feasible default (threshold,
+    groups) is chosen at plan time, every accepted setting assigns all
+    items to the two classes, twisted groups split pairs into single slices
+    (more items than with one-sided sweeps), and device calls are refused."""
+    rng = np.random.default_rng(12)
+    k = 40
+    n_r, n_z = rng.integers(16, 200, size=k), rng.integers(16, 200, size=k)
+    n_t, alpha = rng.choice([8, 16, 32], size=k), rng.uniform(0.05, 1.0, size=k)
+    tw = cyl.BatchPlan(n_r, n_z, n_t, alpha, 1e-3, 1e-13, host_only=True)
+    pl = cyl.BatchPlan(n_r, n_z, n_t, alpha, 1e-3, 1e-13, host_only=True, plain_sweeps=True)
+    thr, G, counts = tw.config()
+    assert G in (1, 2, 4) and sum(counts) > 0
+    accepted = 0
+    for th in (0, 31, 63, 95):
+        for G in (1, 2, 4):
+            for bp in (tw, pl):
+                try:
+                    bp.set_config(th, G)
+                except cyl.CylError as e:
+                    assert e.status == cyl.EINVAL
+                    continue
+                accepted += 1
+                t2, g2, c2 = bp.config()
+                assert (t2, g2) == (th, G) and min(c2) >= 0 and sum(c2) > 0
+    assert accepted >= 8
+    tw.set_config(0, 1)
+    pl.set_config(0, 1)
+    assert tw.config()[2][0] > pl.config()[2][0]
+    import torch
+    x = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises((cyl.CylError, ValueError)):
+        tw.heat_step(x, None, 1)
