@@ -732,6 +732,11 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
           else add_item(2 * k - 1, 2);
         }
       }
+    // largest first (J x class block x slices): with more items than resident CTAs the
+    // hardware hands out CTAs in launch order, so the longest items start first
+    std::stable_sort(KT.items.begin(), KT.items.end(), [](const Item &x, const Item &y) {
+      return (double)x.J * x.M * x.Nz * x.nsl > (double)y.J * y.M * y.Nz * y.nsl;
+    });
     KT.built = true;
   }
   cheb_matrices(m, hp.Wr_f, hp.Wr_i);
