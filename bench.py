@@ -44,6 +44,7 @@ from paper_2206_04827_gb300 import inputs  # noqa: E402
 M = N_Z = P = 128
 ALPHA, DT, NSTEPS, TOL = 1.0, 1e-3, 100, 1e-14
 TOL_512 = 1e-15
+BATCH_PROBLEMS = 256
 SEED = 1001
 METRIC = 'FP64 unknowns*steps/s at <=1e-12 rel err'
 UNIT = 'unknowns*steps/s'
@@ -313,12 +314,12 @@ class Batch256(Workload):
     def __init__(self, cyl, torch, dev, stream, nsteps):
         self.torch, self.cyl, self.stream = torch, cyl, stream
         rng = inputs.rng_for(1003)
-        k = 256
+        k = BATCH_PROBLEMS
         self.n_r = rng.integers(32, 257, size=k)
         self.n_z = rng.integers(32, 257, size=k)
         self.n_t = rng.choice([32, 64, 128], size=k)
         self.alpha = rng.uniform(0.01, 1.0, size=k)
-        self.steps = 50
+        self.steps = 50 if nsteps == NSTEPS else nsteps     # --nsteps shortens it for profiling
         self.bp = cyl.BatchPlan(self.n_r, self.n_z, self.n_t, self.alpha, DT, TOL, stream=stream.cuda_stream)
         g = np.concatenate([inputs.smooth_coeffs(p, m, n, 1.25, rng).ravel() for p, m, n in self.bp.shapes])
         self.g = torch.as_tensor(g, device=dev)
@@ -630,9 +631,13 @@ def main():
     ap.add_argument('--cpu-slices', type=int, default=16)
     ap.add_argument('--cpu-steps', type=int, default=10)
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--batch-problems', type=int, default=256,
+                    help='problems of the batch256 workload (256 = the workload; fewer only for profiling)')
     ap.add_argument('--nsteps', type=int, default=NSTEPS,
                     help='BDF1 steps per bench step of heat128 (100 = the workload; fewer only for profiling)')
     args = ap.parse_args()
+    global BATCH_PROBLEMS
+    BATCH_PROBLEMS = args.batch_problems
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == 'reference':
