@@ -330,8 +330,9 @@ class Batch256(Workload):
         self.launches = 2
         self.kernel = 'adi_batch_kernel'
         thr, G, counts = self.bp.config()
-        self.config = {'workload': '256 heat problems, n_r, n_z ~ U{32..256}, n_theta ~ {32,64,128}, '
-                                   'alpha ~ U[0.01,1], dt 1e-3, 50 BDF1 steps, T0 = 0, smooth forcing (decay 1.25)',
+        self.config = {'workload': '%d heat problems, n_r, n_z ~ U{32..256}, n_theta ~ {32,64,128}, '
+                                   'alpha ~ U[0.01,1], dt 1e-3, %d BDF1 steps, T0 = 0, smooth forcing (decay 1.25)'
+                                   % (k, self.steps),
                        'problems': k, 'unknowns': int(self.bp.N), 'autotuned': {'threshold': thr, 'groups': G,
                                                                              'items_per_class': list(counts)}}
         self.host = None
