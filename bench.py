@@ -144,11 +144,12 @@ def aggregate(t_local, units_local, dist=None, device=None):
     return float(t.item()), float(u.item())
 
 
-def hbm_line(wl, seconds_per_launch):
-    """Where the dominant kernel sits against the HBM roofline: its measured
-    DRAM traffic per launch over its launch time, against the measured copy
-    bandwidth (MEASURED_PEAKS.json, else the 6.8 TB/s fallback)."""
-    if wl.traffic is None or wl.launches != 1:
+def hbm_line(wl, seconds_per_step):
+    """Where the dominant kernel sits against the HBM roofline: its DRAM
+    traffic per bench step over the step time, against the measured copy
+    bandwidth (MEASURED_PEAKS.json, else the 6.8 TB/s fallback) and the
+    nominal 7.9 TB/s."""
+    if wl.traffic is None:
         return None
     peak, basis = 6800.0, 'of fallback'
     try:
@@ -156,8 +157,9 @@ def hbm_line(wl, seconds_per_launch):
             peak, basis = float(json.load(fh)['hbm_gbs']), 'of measured'
     except (OSError, KeyError, ValueError):
         pass
-    gbs = wl.traffic / seconds_per_launch / 1e9
-    return {'achieved_gbs': gbs, 'peak_gbs': peak, 'frac': gbs / peak, 'basis': basis}
+    gbs = wl.traffic / seconds_per_step / 1e9
+    return {'achieved_gbs': gbs, 'peak_gbs': peak, 'frac': gbs / peak, 'basis': basis,
+            'frac_of_nominal_7900': gbs / 7900.0}
 
 
 def adi_flops_per_launch(plan, nsteps):
@@ -174,6 +176,10 @@ class Workload:
     name = ''
     config = {}
     traffic = None
+    traffic_basis = None
+
+    def extra(self, stream, reps):
+        return {}
 
     def reset(self):
         pass
@@ -254,6 +260,25 @@ class Poisson33(Workload):
     def step(self):
         self.plan.poisson(self.f, self.u, self.cyl.VALUES)
 
+    def extra(self, stream, reps):
+        """The same solve in coefficient space only (no value <-> coefficient transforms)."""
+        t = self.torch
+        fc = self.plan.vals2coeffs(self.f, t.empty_like(self.f))
+        uc = t.empty_like(self.f)
+        for _ in range(3):
+            self.plan.poisson(fc, uc, self.cyl.COEFFS)
+        t.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.plan.poisson(fc, uc, self.cyl.COEFFS)
+            e1.record(stream)
+            t.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return {'coeffs_only_value': self.units / (statistics.median(ms) * 1e-3),
+                'coeffs_only_ms': statistics.median(ms)}
+
     def e2e_setup(self):
         t = self.torch
         self.host = (self.f.cpu().pin_memory(), t.empty(self.f.shape, dtype=t.float64).pin_memory())
@@ -327,6 +352,11 @@ class Batch256(Workload):
         self.tune_ms = self.bp.autotune(self.T, self.g, 1)
         self.units = self.bp.N * self.steps
         self.flops = self.bp.flops(self.steps)
+        # DRAM bytes per unknown and step of the batch kernel: 949,844,224 + 392,462,592 bytes for one
+        # step of a 32-problem batch of 43,257,728 unknowns (profiles/adi_batch_kernel_batch256.md); the
+        # traffic (T, g and the right sides per item and step) grows with unknowns x steps
+        self.traffic = (949844224 + 392462592) / 43257728 * self.units
+        self.traffic_basis = 'scaled from one ncu capture (32 problems, 1 step) by unknowns x steps'
         self.launches = 2
         self.kernel = 'adi_batch_kernel'
         thr, G, counts = self.bp.config()
@@ -572,7 +602,7 @@ def run_ours(args):
         'config': dict(wl.config, l2='flushed between timed steps (256 MB write)',
                        parallelism='replicas' if world > 1 else 'single'),
         'roofline': {'bound': 'alu', 'achieved': achieved / 1e12, 'peak': peak / 1e12, 'unit': 'TFLOP/s',
-                     'frac': achieved / peak, 'traffic': wl.traffic,
+                     'frac': achieved / peak, 'traffic': wl.traffic, 'traffic_basis': wl.traffic_basis,
                      'peak_basis': '152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (of derived)',
                      'kernel': wl.kernel, 'hbm': hbm_line(wl, t_sum / args.steps)},
         'e2e': {'value': world * wl.units * len(e2e) / sum(e2e), 'unit': UNIT,
@@ -587,6 +617,7 @@ def run_ours(args):
                                           '(QZ Bartels-Stewart per slice, one process per slice)'
                                           % (len(cpu['slices']), P, args.cpu_steps)}
         line['max_rel_err_vs_oracle'] = acc
+    line.update(wl.extra(stream, 20))
     if isinstance(wl, Batch256):
         plain = wl.plain_rate()
         line['plain_per_problem_value'] = world * plain

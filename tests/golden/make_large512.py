@@ -5,8 +5,8 @@ coefficients.  Inputs: paper_2206_04827_gb300.inputs.smooth_coeffs(512, 512,
 512, decay 1.1) from seed 1002 (the 512^3 workload's generator).  Calls only
 oracle/ (QZ Bartels-Stewart with one step of iterative refinement per solve;
 the plain direct solve drifts to ~1e-11 at this size).  Slices are
-independent, so only the sampled slices are solved.  About 15 minutes on one
-core; run from the repository root:
+independent, so only the sampled slices are solved.  About 25 minutes on an
+8-core host; run from the repository root:
 
     python tests/golden/make_large512.py
 """
@@ -23,7 +23,8 @@ from paper_2206_04827_gb300 import inputs  # noqa: E402
 
 P = M = N = 512
 ALPHA, DT, HSTEPS, SEED = 0.1, 1e-4, 20, 1002
-SLICES = [0, 1, 256, 511]            # wavenumbers 0, 1 (Re), 128 (Im), 256 (Nyquist)
+# wavenumbers 0, 1 (Re), 2 (Im), 127 (Re), 128 (Im), 255 (Re), 256 (Nyquist)
+SLICES = [0, 1, 4, 253, 256, 509, 511]
 # the large coefficients (low indices) densely, then a few far rows / columns
 IDX = sorted(set(range(16)) | {64, 65, 128, 129, 255, 256, 384, 385, 509, 510, 511})
 
