@@ -210,6 +210,7 @@ class Heat128(Workload):
         self.launches = 1
         self.kernel = 'adi_kernel'
         self.traffic = self.TRAFFIC if nsteps == NSTEPS else None
+        self.traffic_basis = 'ncu capture of the bench launch' if self.traffic else None
         self.config = {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF1 steps, '
                                    '8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
                        'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nsteps, 'adi_tol': TOL}
@@ -295,6 +296,10 @@ class Poisson33(Workload):
 
 class Large512(Workload):
     name = 'large512'
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches
+    # (Poisson 102,546,660,096 + 88,557,331,456; 20 heat steps 1,747,276,132,864 + 1,472,403,574,784;
+    # profiles/adi_kernel_large512.md)
+    TRAFFIC = 102546660096 + 88557331456 + 1747276132864 + 1472403574784
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
         m = n = p = 512
@@ -310,6 +315,8 @@ class Large512(Workload):
         self.flops = self.plan.flops(0, 1) + self.plan.flops(1, self.hsteps)
         self.launches = 2
         self.kernel = 'adi_kernel'
+        self.traffic = self.TRAFFIC
+        self.traffic_basis = 'ncu capture of the bench step (two launches)'
         self.config = {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
                                    'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out',
                        'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL_512}
