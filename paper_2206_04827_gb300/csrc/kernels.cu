@@ -978,8 +978,8 @@ cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int b
 //   dL/dg_n = kappa lam;  dL/dalpha += <lam, X_{n+1} - X_n - kappa g_n> / alpha
 // (the last identity follows from A Y B^T + C Y D^T = E, A = C - kappa alpha L,
 // D = -kappa alpha D2:  d/dalpha of the solve is (E - C Y B^T) / alpha).
-template <bool SMEM>
-__global__ void __launch_bounds__(512, 1) adi_adjoint_kernel(const AdiArgs a, AdjointArgs g) {
+template <bool SMEM, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, AdjointArgs g) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ double red[32];
@@ -1310,19 +1310,24 @@ cudaError_t launch_sum_partials(const double *part, int n, double scale, double 
   return cudaGetLastError();
 }
 
+template <bool SMEM, int MAXT>
+static cudaError_t launch_adjoint_t(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(adi_adjoint_kernel<SMEM, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  adi_adjoint_kernel<SMEM, MAXT><<<a.nitems, threads, smem, st>>>(a, g);
+  return cudaGetLastError();
+}
+
+// CTAs of at most 256 threads get the instantiation with the full register budget.
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || g.n_hi <= g.n_lo) return cudaSuccess;
-  cudaError_t e;
-  if (a.use_smem == 2) {
-    e = cudaFuncSetAttribute(adi_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    adi_adjoint_kernel<true><<<a.nitems, threads, smem, st>>>(a, g);
-  } else {
-    e = cudaFuncSetAttribute(adi_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    adi_adjoint_kernel<false><<<a.nitems, threads, smem, st>>>(a, g);
-  }
-  return cudaGetLastError();
+  if (a.use_smem == 2)
+    return threads <= 256 ? launch_adjoint_t<true, 256>(a, g, threads, smem, st)
+                          : launch_adjoint_t<true, 512>(a, g, threads, smem, st);
+  return threads <= 256 ? launch_adjoint_t<false, 256>(a, g, threads, smem, st)
+                        : launch_adjoint_t<false, 512>(a, g, threads, smem, st);
 }
 
 template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
