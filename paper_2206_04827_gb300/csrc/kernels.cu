@@ -3,20 +3,32 @@
 // adi_kernel        one CTA per work item (one or two half-complex slices x one
 //                   radial parity class x one vertical parity class) runs the
 //                   whole time loop of its item: right-hand-side assembly of
-//                   eq. HelmholtzMatEqn, J iterations of Algorithm 1 and the
-//                   Dirichlet expansion X = S_r Y S_z^T, with the work arrays
-//                   resident in shared memory.
+//                   eq. HelmholtzMatEqn (BDF1, or delta^(b) over a history ring
+//                   for BDF b, plus the lifting correction of Dirichlet data),
+//                   J iterations of Algorithm 1 and the Dirichlet expansion
+//                   X = S_r Y S_z^T, with the work arrays resident in shared
+//                   memory where they fit.
+// adi_batch_kernel  the same per item, for many problems: persistent CTAs of G
+//                   thread groups pull items (largest first) from a queue.
+// adi_adjoint_kernel  the transposed step map run backward over the steps
+//                   (BDF1, or the multistep ring of BDF b).
 // axis_matvec       dense value <-> coefficient transform along one axis
 //                   (Section 2: DCT-I in r and z, DFT in theta).
+// disk_poisson      the horizontal (disk) Poisson solve of Section 4.
+// lift_*, permute_slots, sum_partials   boundary-data lifting, history / ring
+//                   reordering, reduction of the per-item alpha-gradient parts.
 //
 // GB300 facts that shape the ADI kernel: FP64 runs at 2 FMA/clk/SM (one warp
-// instruction occupies an SM sub-partition's FP64 pipe for 64 cycles), so a
-// single warp per sub-partition saturates the pipe even on a dependent chain,
-// and memory traffic is an order of magnitude below the arithmetic time.  The
-// kernel therefore minimises FP64 instructions per element (12 in the radial
-// sweep, 8 in the vertical sweep, see plan.hpp for the pre-scaled factors)
-// and keeps every sweep sequential per thread: a thread owns one column in
-// the radial phase and one row in the vertical phase.
+// instruction occupies an SM sub-partition's FP64 pipe for 64 cycles) and the
+// ADI work is an order of magnitude above the memory traffic, so the kernel
+// minimises FP64 instructions per element (12 in the radial sweep, 8 in the
+// vertical sweep, see plan.hpp for the pre-scaled factors) and keeps each
+// banded solve sequential per thread.  A lone dependent FMA chain reaches the
+// 64-cycle interval, but with the shared-memory loads around it one warp per
+// sub-partition keeps the pipe busy only about 80 % of the time; a second warp
+// lifts that to about 95 %.  Where a sweep has too few chains for two warps
+// per sub-partition (grids up to about 130), each solve is split in two
+// (twisted sweeps below), two threads per chain.
 #include <cstdio>
 
 #include <algorithm>
