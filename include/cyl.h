@@ -412,13 +412,16 @@ cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int pari
 /* Host copy of one work item's factor records for ADI iteration j (the
  * tables the kernels read; layout in the library's plan header: radial
  * records of 12 doubles per class row, vertical records of 8 per class
- * column, plus the interface maps of twisted solves).  info[8] receives
- * {M, Nz, J, twr, twz, k, parity_r, parity_z}; twr / twz are the split rows of
- * the twisted radial / vertical solves (0: plain LU sweep).  radial needs
- * M*12 + (twr ? 24 : 0) doubles, vertical Nz*8 + (twz ? 16 : 0); either may
- * be NULL.  Items are numbered as the plan lists them (which as above). */
-cyl_status cyl_plan_item_tables(cyl_plan_t plan, int which, int item, int j, int *info, double *radial,
-                                double *vertical);
+ * column, plus the interface maps of twisted solves).  transposed = 1 gives
+ * the records of the transposed system the adjoint kernels solve (heat kinds
+ * only, else CYL_ESTATE; always one-sided).  info[8] receives {M, Nz, J, twr,
+ * twz, k, parity_r, parity_z}; twr / twz are the split rows of the twisted
+ * radial / vertical solves (0: plain LU sweep).  radial needs M*12 + (twr and
+ * not transposed ? 24 : 0) doubles, vertical Nz*8 + (twz and not transposed ?
+ * 16 : 0); either may be NULL.  Items are numbered as the plan lists them
+ * (which as above). */
+cyl_status cyl_plan_item_tables(cyl_plan_t plan, int which, int item, int j, int transposed, int *info,
+                                double *radial, double *vertical);
 
 /* Grid of Definition "grid" (Section 2) into caller-owned HOST arrays:
  * r[m] = cos((m-1-j) pi / (m-1)), z[n] likewise, theta[p] = (2l - p) pi / p.

@@ -895,8 +895,8 @@ cyl_status cyl_plan_shifts(cyl_plan_t P, int which, int k, int parity, int *J, d
   return CYL_OK;
 }
 
-cyl_status cyl_plan_item_tables(cyl_plan_t P, int which, int item, int j, int *info, double *radial,
-                                double *vertical) {
+cyl_status cyl_plan_item_tables(cyl_plan_t P, int which, int item, int j, int transposed, int *info,
+                                double *radial, double *vertical) {
   if (!P || !info || which < 0 || which >= cyl::kNumKinds || item < 0 || j < 0) return CYL_EINVAL;
   if (P->is_batch) return CYL_ESTATE;
   const auto &KT = P->hp.kind[which];
@@ -906,11 +906,14 @@ cyl_status cyl_plan_item_tables(cyl_plan_t P, int which, int item, int j, int *i
   if (j >= it.J) return CYL_EINVAL;
   info[0] = it.M; info[1] = it.Nz; info[2] = it.J; info[3] = it.twr; info[4] = it.twz;
   info[5] = it.k; info[6] = it.pr; info[7] = it.pz;
-  const size_t rs = (size_t)it.M * cyl::RSTRIDE + (it.twr ? cyl::RTWIST : 0);
-  const size_t zs = (size_t)it.Nz * cyl::ZSTRIDE + (it.twz ? cyl::ZTWIST : 0);
+  if (transposed && (it.roffT < 0 || it.zoffT < 0)) return CYL_ESTATE;
+  // the transposed (adjoint) tables are one-sided: no interface maps
+  const size_t rs = (size_t)it.M * cyl::RSTRIDE + (!transposed && it.twr ? cyl::RTWIST : 0);
+  const size_t zs = (size_t)it.Nz * cyl::ZSTRIDE + (!transposed && it.twz ? cyl::ZTWIST : 0);
   const double *F = P->hp.factors.data();
-  if (radial) std::memcpy(radial, F + it.roff + (size_t)j * rs, rs * sizeof(double));
-  if (vertical) std::memcpy(vertical, F + it.zoff + (size_t)j * zs, zs * sizeof(double));
+  const long long ro = transposed ? it.roffT : it.roff, zo = transposed ? it.zoffT : it.zoff;
+  if (radial) std::memcpy(radial, F + ro + (size_t)j * rs, rs * sizeof(double));
+  if (vertical) std::memcpy(vertical, F + zo + (size_t)j * zs, zs * sizeof(double));
   return CYL_OK;
 }
 

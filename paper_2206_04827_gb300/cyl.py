@@ -38,8 +38,8 @@ _sig = {
                                             ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_bdf_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       ctypes.POINTER(ctypes.c_size_t)]),
-    'cyl_plan_item_tables': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                            _c_double_p, _c_double_p]),
+    'cyl_plan_item_tables': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int), _c_double_p, _c_double_p]),
     'cyl_disk_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     'cyl_destroy': (ctypes.c_int, [_vp]),
     'cyl_vals2coeffs': (ctypes.c_int, [_vp, _vp, _vp]),
@@ -258,14 +258,16 @@ class Plan:
         _check(_lib.cyl_plan_shifts(self._h, which, k, parity, ctypes.byref(J), iv, ps, qs), 'cyl_plan_shifts')
         return J.value, tuple(iv), np.array(ps), np.array(qs)
 
-    def item_tables(self, which, item, j):
-        """(info dict, radial records, vertical records) of one item's ADI iteration j."""
+    def item_tables(self, which, item, j, transposed=False):
+        """(info dict, radial records, vertical records) of one item's ADI iteration j
+        (of the transposed system of the adjoint when transposed)."""
         info = (ctypes.c_int * 8)()
-        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, info, None, None), 'cyl_plan_item_tables')
+        tr = int(bool(transposed))
+        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, tr, info, None, None), 'cyl_plan_item_tables')
         M, Nz, J, twr, twz = info[0], info[1], info[2], info[3], info[4]
-        rad = (ctypes.c_double * (M * 12 + (24 if twr else 0)))()
-        ver = (ctypes.c_double * (Nz * 8 + (16 if twz else 0)))()
-        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, info, rad, ver), 'cyl_plan_item_tables')
+        rad = (ctypes.c_double * (M * 12 + (24 if twr and not tr else 0)))()
+        ver = (ctypes.c_double * (Nz * 8 + (16 if twz and not tr else 0)))()
+        _check(_lib.cyl_plan_item_tables(self._h, which, item, j, tr, info, rad, ver), 'cyl_plan_item_tables')
         keys = ('M', 'Nz', 'J', 'twr', 'twz', 'k', 'pr', 'pz')
         return dict(zip(keys, list(info))), np.array(rad), np.array(ver)
 
