@@ -461,26 +461,28 @@ class Adjoint128(Workload):
         self.dT0 = torch.empty_like(self.T0)
         self.dg = torch.empty_like(self.g)
         self.dal = torch.zeros(1, dtype=torch.float64, device=dev)
-        nb = self.plan.adjoint_workspace_bytes(self.steps, self.every, True)
+        nb = self.plan.adjoint_workspace_bytes(self.steps, self.every, True, have_ckpt=True)
         self.ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device=dev)
         Nn = M * N_Z * P
+        self.ck = torch.empty((self.steps // self.every + 1) * Nn, dtype=torch.float64, device=dev)
         self.units = Nn * self.steps
-        # forward + checkpoint pass + recompute pass (heat kernel) and the transposed pass
-        self.flops = 3 * self.plan.flops(1, self.steps) + self.plan.flops(1, self.steps, transposed=True)
-        self.launches = 1 + 1 + 2 * (self.steps // self.every) + 1
+        # forward run (writing the checkpoints) + recompute pass (heat kernel) and the transposed pass
+        self.flops = 2 * self.plan.flops(1, self.steps) + self.plan.flops(1, self.steps, transposed=True)
+        self.launches = 1 + 2 * (self.steps // self.every) + 1
         self.kernel = 'adi_kernel + adi_adjoint_kernel'
         self.config = {'workload': 'adjoint 128^3, alpha 0.5, dt 1e-3, 200 BDF1 steps, checkpoint every 20: '
-                                   'forward run + gradients of |T_N - T_target|^2 in T0, space-time g and alpha',
+                                   'forward run (writing the checkpoints) + gradients of |T_N - T_target|^2 in T0, '
+                                   'space-time g and alpha',
                        'n_r': M, 'n_z': N_Z, 'n_theta': P, 'units': 'unknowns x 200 steps per gradient evaluation'}
         self.host = None
 
     def step(self):
         N = M * N_Z * P
         self.T.copy_(self.T0)
-        self.plan.heat_step(self.T, self.g, self.steps, g_step_stride=N)
+        self.plan.heat_step(self.T, self.g, self.steps, g_step_stride=N, ckpt=self.ck, ckpt_every=self.every)
         lam = 2.0 * self.w * (self.T - self.tgt)
         self.plan.heat_adjoint(self.T0, self.g, self.steps, lam, self.dT0, self.dg, self.dal, g_step_stride=N,
-                               ckpt_every=self.every, workspace=self.ws)
+                               ckpt_every=self.every, workspace=self.ws, ckpt=self.ck)
 
     def e2e_setup(self):
         t = self.torch

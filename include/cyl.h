@@ -279,13 +279,19 @@ cyl_status cyl_heat_adjoint(cyl_plan_t plan, const double *T0, const double *g,
 /* cyl_heat_adjoint_bc -- cyl_heat_adjoint of the run cyl_heat_step_bc(T0, g,
  * g_step_stride, nsteps, bc) computes.  The data enter that run affinely, so
  * dL/dT0 and dL/dg are those of the zero-data run; the alpha identity holds
- * on the lifted states, which the recomputation produces with bc. */
+ * on the lifted states, which the recomputation produces with bc.
+ *   ckpt   NULL, or the checkpoints that forward run wrote (its ckpt argument
+ *          with the same ckpt_every): the adjoint then reads them instead of
+ *          recomputing them in a forward pass of its own (one forward pass
+ *          fewer), and needs the smaller workspace of need_alpha = 2. */
 cyl_status cyl_heat_adjoint_bc(cyl_plan_t plan, const double *T0, const double *g,
                                long long g_step_stride, int nsteps, const double *bc, int ckpt_every,
-                               const double *dL_dTN, double *dL_dT0, double *dL_dg,
+                               const double *ckpt, const double *dL_dTN, double *dL_dT0, double *dL_dg,
                                double *dL_dalpha, void *workspace, size_t workspace_bytes);
 
-/* Bytes of device workspace cyl_heat_adjoint needs (0 when need_alpha is 0). */
+/* Bytes of device workspace cyl_heat_adjoint needs: need_alpha 0 (no dL/dalpha)
+ * needs none, 1 the checkpoints and one recomputed segment, 2 (dL/dalpha with
+ * the caller's checkpoints, cyl_heat_adjoint_bc) one recomputed segment. */
 cyl_status cyl_heat_adjoint_workspace(cyl_plan_t plan, int nsteps, int ckpt_every, int need_alpha,
                                       size_t *bytes);
 

@@ -46,22 +46,24 @@ class HeatRun(torch.autograd.Function):
         stride = 0 if (gc is None or gc.dim() == 3) else p * m * n
         bcc = bc.contiguous() if bc is not None else None
         T = T0c.clone()
-        plan.heat_step(T, gc, nsteps, g_step_stride=stride, bc=bcc)
+        # checkpoints of the forward run, read back by the adjoint (no second forward pass)
+        ck = torch.empty((nsteps // ckpt_every + 1) * p * m * n, dtype=torch.float64, device=T0.device)
+        plan.heat_step(T, gc, nsteps, g_step_stride=stride, bc=bcc, ckpt=ck, ckpt_every=ckpt_every)
         empty = torch.empty(0, device=T0.device)
-        ctx.save_for_backward(T0c, gc if gc is not None else empty, bcc if bcc is not None else empty)
+        ctx.save_for_backward(T0c, gc if gc is not None else empty, bcc if bcc is not None else empty, ck)
         ctx.meta = (plan, nsteps, ckpt_every, stride, g is not None, bc is not None)
         return T
 
     @staticmethod
     def backward(ctx, dT):
-        T0, gsaved, bcsaved = ctx.saved_tensors
+        T0, gsaved, bcsaved, ck = ctx.saved_tensors
         plan, nsteps, ckpt_every, stride, has_g, has_bc = ctx.meta
         g = gsaved if has_g else None
         dT0 = torch.empty_like(T0)
         dg = torch.empty_like(g) if (has_g and ctx.needs_input_grad[1]) else None
         dal = torch.zeros(1, dtype=torch.float64, device=T0.device) if ctx.needs_input_grad[2] else None
         plan.heat_adjoint(T0, g, nsteps, dT.contiguous(), dT0, dg, dal, g_step_stride=stride,
-                          ckpt_every=ckpt_every, bc=bcsaved if has_bc else None)
+                          ckpt_every=ckpt_every, bc=bcsaved if has_bc else None, ckpt=ck)
         return (dT0, dg, dal.reshape(()) if dal is not None else None, None, None, None, None, None)
 
 

@@ -736,36 +736,38 @@ cyl_status cyl_heat_adjoint_bdf(cyl_plan_t P, const double *hist0, int nvalid, c
   return CYL_OK;
 }
 
-static size_t adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, bool need_alpha) {
+// need_alpha: 0 none, 1 with the library's own checkpoints, 2 with the caller's (cyl_heat_step's ckpt)
+static size_t adjoint_workspace_doubles(const cyl_plan_s *P, int nsteps, int ckpt_every, int need_alpha) {
   if (!need_alpha || nsteps <= 0) return 0;
   const long long c = std::min(ckpt_every, nsteps);
   const long long nseg = (nsteps + c - 1) / c;
-  // checkpoints X_0, X_c, ..., one segment of states X_{s c} .. X_{s c + c}, one work state
-  return (size_t)(nseg + (c + 1) + 1) * P->N;
+  // checkpoints X_0, X_c, ... (unless the caller's), one segment of states X_{s c} .. X_{s c + c}, one work state
+  return (size_t)((need_alpha == 2 ? 0 : nseg) + (c + 1) + 1) * P->N;
 }
 
 cyl_status cyl_heat_adjoint_workspace(cyl_plan_t P, int nsteps, int ckpt_every, int need_alpha, size_t *bytes) {
   if (!P || !bytes || nsteps < 0 || ckpt_every < 1) return CYL_EINVAL;
-  *bytes = adjoint_workspace_doubles(P, nsteps, ckpt_every, need_alpha != 0) * sizeof(double);
+  if (need_alpha < 0 || need_alpha > 2) return CYL_EINVAL;
+  *bytes = adjoint_workspace_doubles(P, nsteps, ckpt_every, need_alpha) * sizeof(double);
   return CYL_OK;
 }
 
 cyl_status cyl_heat_adjoint(cyl_plan_t P, const double *T0, const double *g, long long g_step_stride, int nsteps,
                             int ckpt_every, const double *dL_dTN, double *dL_dT0, double *dL_dg,
                             double *dL_dalpha, void *workspace, size_t workspace_bytes) {
-  return cyl_heat_adjoint_bc(P, T0, g, g_step_stride, nsteps, nullptr, ckpt_every, dL_dTN, dL_dT0, dL_dg,
-                             dL_dalpha, workspace, workspace_bytes);
+  return cyl_heat_adjoint_bc(P, T0, g, g_step_stride, nsteps, nullptr, ckpt_every, nullptr, dL_dTN, dL_dT0,
+                             dL_dg, dL_dalpha, workspace, workspace_bytes);
 }
 
 cyl_status cyl_heat_adjoint_bc(cyl_plan_t P, const double *T0, const double *g, long long g_step_stride,
-                               int nsteps, const double *bc, int ckpt_every, const double *dL_dTN,
+                               int nsteps, const double *bc, int ckpt_every, const double *ckpt, const double *dL_dTN,
                                double *dL_dT0, double *dL_dg, double *dL_dalpha, void *workspace,
                                size_t workspace_bytes) {
   if (!P || !dL_dTN || !dL_dT0 || nsteps < 0 || ckpt_every < 1 || g_step_stride < 0) return CYL_EINVAL;
   if (g_step_stride != 0 && (size_t)g_step_stride < P->N) return CYL_EINVAL;
   if (dL_dalpha && !T0) return CYL_EINVAL;
   if (P->host_only || P->is_batch || !P->hp.kind[1].built) return CYL_ESTATE;
-  const size_t need = adjoint_workspace_doubles(P, nsteps, ckpt_every, dL_dalpha != nullptr);
+  const size_t need = adjoint_workspace_doubles(P, nsteps, ckpt_every, !dL_dalpha ? 0 : (ckpt ? 2 : 1));
   if (need && (!workspace || workspace_bytes < need * sizeof(double))) return CYL_EINVAL;
   const size_t N = P->N;
   const double kappa = P->hp.dt;
@@ -794,18 +796,23 @@ cyl_status cyl_heat_adjoint_bc(cyl_plan_t P, const double *T0, const double *g, 
   }
   const int c = std::min(ckpt_every, nsteps);
   const int nseg = (nsteps + c - 1) / c;
-  double *ck = static_cast<double *>(workspace);       // nseg slots
-  double *seg = ck + (size_t)nseg * N;                  // c + 1 slots
+  // checkpoints (slot s = X_{s c}): the caller's, written by cyl_heat_step with the same ckpt_every,
+  // or computed here by a forward pass
+  double *own_ck = ckpt ? nullptr : static_cast<double *>(workspace);          // nseg slots
+  const double *ck = ckpt ? ckpt : own_ck;
+  double *seg = ckpt ? static_cast<double *>(workspace) : own_ck + (size_t)nseg * N;   // c + 1 slots
   double *work = seg + (size_t)(c + 1) * N;             // 1 slot
-  e = cudaMemcpyAsync(ck, T0, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
-  if (e != cudaSuccess) return from_cuda(e);
   cyl_status s;
   // the data enter the run affinely: only the recomputed states see them
   if (bc && (s = prepare_lift(P, 1, bc)) != CYL_OK) return s;
   const bool lifted = bc != nullptr;
-  if (nseg > 1) {                                       // checkpoints X_c, X_2c, ... (ck slot s = X_{s c})
-    s = run_adi(P, 1, T0, work, g, kappa, g ? g_step_stride : 0, (nseg - 1) * c, ck, c, lifted);
-    if (s != CYL_OK) return s;
+  if (!ckpt) {
+    e = cudaMemcpyAsync(own_ck, T0, N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (nseg > 1) {                                     // checkpoints X_c, X_2c, ...
+      s = run_adi(P, 1, T0, work, g, kappa, g ? g_step_stride : 0, (nseg - 1) * c, own_ck, c, lifted);
+      if (s != CYL_OK) return s;
+    }
   }
   adj.traj = seg;
   adj.alpha_part = P->d_apart;

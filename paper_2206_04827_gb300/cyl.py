@@ -50,7 +50,7 @@ _sig = {
     'cyl_heat_adjoint': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                         _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_bc': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int, _vp, ctypes.c_int, _vp,
-                                           _vp, _vp, _vp, _vp, ctypes.c_size_t]),
+                                           _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_size_t)]),
     'cyl_status_string': (ctypes.c_char_p, [ctypes.c_int]),
@@ -209,22 +209,27 @@ class Plan:
                'cyl_heat_adjoint_bdf')
         return dL_dhist0
 
-    def adjoint_workspace_bytes(self, nsteps, ckpt_every, need_alpha):
+    def adjoint_workspace_bytes(self, nsteps, ckpt_every, need_alpha, have_ckpt=False):
+        mode = 0 if not need_alpha else (2 if have_ckpt else 1)
         nb = ctypes.c_size_t()
-        _check(_lib.cyl_heat_adjoint_workspace(self._h, int(nsteps), int(ckpt_every), int(bool(need_alpha)),
-                                               ctypes.byref(nb)), 'cyl_heat_adjoint_workspace')
+        _check(_lib.cyl_heat_adjoint_workspace(self._h, int(nsteps), int(ckpt_every), mode, ctypes.byref(nb)),
+               'cyl_heat_adjoint_workspace')
         return nb.value
 
     def heat_adjoint(self, T0, g, nsteps, dL_dTN, dL_dT0, dL_dg=None, dL_dalpha=None, g_step_stride=0,
-                     ckpt_every=1, workspace=None, bc=None):
-        """Reverse-mode gradients of the BDF1 run (see include/cyl.h: cyl_heat_adjoint).
-        The workspace tensor is allocated here (torch) when not given."""
-        nbytes = self.adjoint_workspace_bytes(nsteps, ckpt_every, dL_dalpha is not None)
+                     ckpt_every=1, workspace=None, bc=None, ckpt=None):
+        """Reverse-mode gradients of the BDF1 run (see include/cyl.h: cyl_heat_adjoint, _bc).
+        ckpt: the checkpoints the forward run wrote with the same ckpt_every (saves
+        the adjoint's own checkpoint pass).  The workspace tensor is allocated here
+        (torch) when not given."""
+        nbytes = self.adjoint_workspace_bytes(nsteps, ckpt_every, dL_dalpha is not None, ckpt is not None)
+        nck = (int(nsteps) // int(ckpt_every) + 1) * self.N
         if nbytes and workspace is None:
             import torch
             workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=dL_dT0.device)
         _check(_lib.cyl_heat_adjoint_bc(self._h, _ptr(T0, 'T0', self.N), _ptr(g, 'g', self.N), int(g_step_stride),
-                                     int(nsteps), _ptr(bc, 'bc', self.N), int(ckpt_every), _ptr(dL_dTN, 'dL_dTN', self.N),
+                                     int(nsteps), _ptr(bc, 'bc', self.N), int(ckpt_every), _ptr(ckpt, 'ckpt', nck),
+                                     _ptr(dL_dTN, 'dL_dTN', self.N),
                                      _ptr(dL_dT0, 'dL_dT0', self.N), _ptr(dL_dg, 'dL_dg', self.N),
                                      _ptr(dL_dalpha, 'dL_dalpha', 1),
                                      _ptr(workspace, 'workspace', (nbytes + 7) // 8) if nbytes else None,

@@ -4,7 +4,7 @@ differences of the GPU forward; plus the torch.autograd wrapper."""
 import numpy as np
 import pytest
 
-from oracle import heat as oheat
+from oracle import heat as oheat, transforms as otr
 from paper_2206_04827_gb300 import inputs
 
 torch = pytest.importorskip('torch')
@@ -202,3 +202,34 @@ def test_adjoint_full_size_128_200_steps(cyl):
     ha = 1e-4 * alpha
     fd = (loss(a=alpha + ha)[0] - loss(a=alpha - ha)[0]) / (2 * ha)
     assert abs(fd - dal.item()) <= TOL_GRAD * abs(fd)
+
+
+@pytest.mark.parametrize('steps,every,wall', [(12, 4, False), (13, 5, False), (9, 3, True), (6, 6, False)])
+def test_forward_checkpoints_give_identical_gradients(cyl, steps, every, wall):
+    """The adjoint fed with the checkpoints its forward run wrote (cyl_heat_step's
+    ckpt, same ckpt_every) skips its own checkpoint pass and returns the same
+    gradients bit for bit (the states come from the same kernel arithmetic),
+    with the smaller workspace."""
+    p, m, n = 8, 17, 15
+    alpha, dt = 0.45, 0.01
+    X0, g, lamN = _problem(p, m, n, steps, 70 + steps, True)
+    bc = dev(otr.coeffs2vals(inputs.smooth_coeffs(p, m, n, 1.2, np.random.default_rng(steps)))) if wall else None
+    plan = cyl.Plan(m, n, p, alpha, dt, 1e-14, poisson=False, heat=True)
+    N = p * m * n
+    T = dev(X0)
+    ck = torch.empty((steps // every + 1) * N, dtype=torch.float64, device='cuda')
+    plan.heat_step(T, dev(g), steps, g_step_stride=N, ckpt=ck, ckpt_every=every, bc=bc)
+    outs = []
+    for ckpt in (None, ck):
+        dT0 = torch.empty(p, m, n, dtype=torch.float64, device='cuda')
+        dg = torch.empty(g.shape, dtype=torch.float64, device='cuda')
+        dal = torch.zeros(1, dtype=torch.float64, device='cuda')
+        nb = plan.adjoint_workspace_bytes(steps, every, True, have_ckpt=ckpt is not None)
+        ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device='cuda')
+        plan.heat_adjoint(dev(X0), dev(g), steps, dev(lamN), dT0, dg, dal, g_step_stride=N, ckpt_every=every,
+                          workspace=ws, bc=bc, ckpt=ckpt)
+        plan.sync()
+        outs.append((dT0, dg, dal))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    assert plan.adjoint_workspace_bytes(steps, every, True, True) < plan.adjoint_workspace_bytes(steps, every, True)
