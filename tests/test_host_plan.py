@@ -396,3 +396,24 @@ def test_transposed_item_tables_drive_adi_to_the_direct_solve(cyl, which):
     with pytest.raises(cyl.CylError) as ei:
         cyl.Plan(m, n, p, host_only=True).item_tables(0, 0, 0, transposed=True)
     assert ei.value.status == cyl.ESTATE
+
+
+@pytest.mark.parametrize('k', [0, 1, 2, 5])
+def test_pencil_spectra_are_the_dirichlet_eigenvalues(cyl, k):
+    """The radial pencil of the Poisson step (A = -L_k against the R_2 block
+    C) has as its smallest eigenvalue the first Dirichlet eigenvalue of the
+    disk mode, j_{k,1}^2 (Bessel zero), and the vertical pencil (D = -D2
+    against the C02 block B) pi^2 / 4; the plan's padded intervals enclose
+    both (the spectra behind the shift choice of Algorithm 1)."""
+    m, n, p = 64, 48, 16
+    ms = sy.ModeSystem(m, n, k, 'poisson')
+    A, C, B, D = _blocks(ms, k % 2, 0)
+    mu = np.sort(np.linalg.eigvals(np.linalg.solve(C, A)).real)
+    nu = np.sort(np.linalg.eigvals(np.linalg.solve(B, D)).real)     # D = -D2 for Poisson
+    j1 = special.jn_zeros(k, 1)[0]
+    assert abs(mu[0] - j1 ** 2) < 1e-9 * j1 ** 2
+    assert abs(nu[0] - np.pi ** 2 / 4) < 1e-9
+    plan = cyl.Plan(m, n, p, poisson=True, host_only=True)
+    _, (a, b, c, d), _, _ = plan.shifts(0, k, k % 2)
+    assert a <= j1 ** 2 <= b and a >= 0.9 * j1 ** 2
+    assert c <= -np.pi ** 2 / 4 <= d and d <= -0.9 * np.pi ** 2 / 4
