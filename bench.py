@@ -1,28 +1,33 @@
 """Benchmark: FP64 unknowns*steps/s of the CCF cylinder solver on one GB300.
 
-Default workload (--workload heat128, one bench step): the 128^3 heat problem,
-n_r = n_z = n_theta = 128, alpha = 1, dt = 1e-3, 100 BDF1 steps, T0 = 8
-Bessel x sine eigenmodes with seeded N(0,1) amplitudes, g = seeded smooth
-CCF coefficients N(0,1) * 1.25^-(i+j+|k|).  value = N * 100 * K / (sum of the
-K timed step durations).  The 16.8 MB fields sit below the 129 MB L2, so L2
-is flushed (a 256 MB write) between timed steps.
+Default workload (--workload large512, one bench step): the 512^3 problem,
+n_r = n_z = n_theta = 512 (1.34e8 unknowns): one Poisson solve -lap u = f
+with f = seeded smooth CCF coefficients N(0,1) * 1.1^-(i+j+|k|), then 20
+BDF1 heat steps (alpha 0.1, dt 1e-4, forcing f) from its solution, in
+coefficient space; ADI tolerance 1e-15.  value = N * 21 * K / (sum of the K
+timed step durations).  Each field (1.07 GB) is far larger than the 129 MB
+L2.  Accuracy: the final state and a Poisson solve against the oracle's
+stored values on sampled slices and coefficients
+(tests/golden/large512_sampled.npz).
 
 Other workloads (same JSON line, for the other problem sizes of the method):
+  heat128     128^3 heat problem, alpha 1, dt 1e-3, 100 BDF1 steps, T0 = 8
+              Bessel x sine eigenmodes, g = smooth coefficients (decay 1.25);
+              L2 flushed (a 256 MB write) between timed steps
   poisson33   -lap u = f on 33 x 33 x 32, manufactured u, values in / out
-  large512    512^3: one Poisson solve + 20 heat steps (alpha 0.1, dt 1e-4)
   batch256    256 heat problems, n_r, n_z ~ U{32..256}, n_theta in {32,64,128},
               alpha ~ U[0.01,1], dt 1e-3, 50 steps, T0 = 0; the plain
               per-problem form is timed beside the batched form
   adjoint128  128^3, alpha 0.5, dt 1e-3, 200 steps, checkpoint every 20:
               forward run + adjoint (gradients in T0, space-time g, alpha)
-  heat128_bdf4  the default problem under BDF 4 (100 steps from T0 alone: the
-              first three steps start up through BDF 1-3)
+  heat128_bdf4  the 128^3 heat problem under BDF 4 (100 steps from T0 alone:
+              the first three steps start up through BDF 1-3)
 
 Legs: --impl ours (default) times the CUDA path through the C ABI; --impl
 reference times the FP64 CPU oracle on the host cores on a bounded sample of
-the same workload (slices of the 128^3 field; slices are independent).
-Under torchrun each rank runs its own replica (independent problems, weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
+the same workload (sampled theta-slices; slices are independent).  Under
+torchrun each rank runs its own replica (independent problems, weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
 """
 import argparse
 import json
@@ -43,30 +48,47 @@ from paper_2206_04827_gb300 import inputs  # noqa: E402
 
 M = N_Z = P = 128
 ALPHA, DT, NSTEPS, TOL = 1.0, 1e-3, 100, 1e-14
+L512, ALPHA_512, DT_512, HSTEPS_512, SEED_512 = 512, 0.1, 1e-4, 20, 1002
 TOL_512 = 1e-15
 BATCH_PROBLEMS = 256
 SEED = 1001
-METRIC = 'FP64 unknowns*steps/s at <=1e-12 rel err'
-UNIT = 'unknowns*steps/s'
+METRIC = 'FP64 unknowns\u00b7steps/s at \u22641e-12 rel err (fwd, adjoint); % of HBM roofline'
+UNIT = 'unknowns\u00b7steps/s'
 SM_COUNT = 152
-FP64_FMA_PER_CLK_PER_SM = 2      # measured: 1192 GFLOP/s at 1980 MHz on 152 SMs
+FP64_FMA_PER_CLK_PER_SM = 2      # the FP64 pipe's issue rate, confirmed live by cyl_fp64_fma_probe
+GOLD512 = os.path.join(ROOT, 'tests', 'golden', 'large512_sampled.npz')
 
 
-# ----------------------------------------------------------------- CPU oracle leg
+def source_hash():
+    """Short hash of the CUDA/C++ sources of libcyl: DRAM-traffic figures taken
+    from an ncu capture are valid only for the kernel source they were taken
+    on, and are reported as stale once it changes."""
+    import hashlib
+    d = os.path.join(ROOT, 'paper_2206_04827_gb300', 'csrc')
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith(('.cu', '.cuh', '.cpp', '.hpp')):
+            with open(os.path.join(d, f), 'rb') as fh:
+                h.update(f.encode() + b'\0' + fh.read())
+    with open(os.path.join(ROOT, 'include', 'cyl.h'), 'rb') as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+BLAS_THREAD_VARS = ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS', 'BLIS_NUM_THREADS')
+
+
 def _host_inputs_coeffs(rng):
-    """Smooth seeded coefficients used by the CPU legs (the CPU legs time
-    throughput on the 128^3 heat workload's shapes and parameters)."""
+    """Smooth seeded coefficients of the 128^3 heat workload's CPU legs."""
     X0 = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
     g = inputs.smooth_coeffs(P, M, N_Z, 1.25, rng)
     return X0, g
 
 
-BLAS_THREAD_VARS = ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS', 'BLIS_NUM_THREADS')
-
-
-def _oracle_worker(args):
-    """One oracle run on a subset of slices (runs in a spawned process whose
-    BLAS was loaded single-threaded, see run_oracle_sample)."""
+def _oracle_worker_128(args):
+    """One oracle run on a subset of the 128^3 heat workload's slices (in a
+    spawned process whose BLAS was loaded single-threaded)."""
     sys.path.insert(0, ROOT)
     from oracle import heat as oheat
     slices, steps = args
@@ -76,36 +98,78 @@ def _oracle_worker(args):
     return time.perf_counter() - t0, {s: out[s] for s in slices}
 
 
-def run_oracle_sample(nslices=16, steps=8, procs=None):
-    """Time the oracle as it stands on `nslices` slices x `steps` steps of the
-    128^3 heat workload, one slice per spawned process (BLAS single-threaded)."""
-    procs = procs or os.cpu_count() or 1
-    sl = [int(s) for s in np.linspace(0, P - 1, nslices).round()]
-    ctx = mp.get_context('spawn')
-    # the children read these when their BLAS loads (at import, before any worker code runs): one
-    # thread per process, so that the processes do not oversubscribe the cores
-    saved = {v: os.environ.get(v) for v in BLAS_THREAD_VARS}
-    for v in BLAS_THREAD_VARS:
-        os.environ[v] = '1'
-    try:
-        t0 = time.perf_counter()
-        with ctx.Pool(processes=min(procs, nslices)) as pool:
-            res = pool.map(_oracle_worker, [([s], steps) for s in sl])
-        wall = time.perf_counter() - t0
-    finally:
-        for v, val in saved.items():
-            if val is None:
-                os.environ.pop(v, None)
-            else:
-                os.environ[v] = val
-    out = {}
-    for _, d in res:
-        out.update(d)
-    # throughput of the worker cores: the summed solve time of all slices spread over the workers
-    # (process start-up, imports and input generation excluded)
-    workers = min(procs, nslices)
-    busy = sum(t for t, _ in res) / workers
-    return nslices * M * N_Z * steps / busy, busy, workers, sl, out
+def _oracle_worker_512(args):
+    """One slice of the 512^3 workload through the oracle: the Poisson solve,
+    then `steps` BDF1 heat steps from its solution.  The worker gets only its
+    slice of f; the other slices of the (lazily allocated) full-size arrays
+    stay zero and are never solved (slices are independent)."""
+    sys.path.insert(0, ROOT)
+    from oracle import heat as oheat
+    s, fs, steps = args
+    F = np.zeros((L512, L512, L512))
+    F[s] = fs
+    t0 = time.perf_counter()
+    u = oheat.poisson(F, slices=[s])
+    T = oheat.heat_steps(u, F, ALPHA_512, DT_512, steps, slices=[s])
+    return time.perf_counter() - t0, {s: T[s].copy()}
+
+
+class OracleSampler:
+    """The oracle as it stands, timed on the host cores over a bounded sample
+    of a workload: one sampled theta-slice per task, tasks spread over
+    spawned single-threaded worker processes (one per core), throughput =
+    sampled unknowns*steps / (summed solve time / workers); process start-up,
+    imports and input generation excluded."""
+
+    def __init__(self, workload, nslices, steps, procs=None, f512=None):
+        self.workload, self.steps = workload, steps
+        self.procs = min(procs or os.cpu_count() or 1, nslices)
+        if workload == 'large512':
+            self.L = L512
+            self.slices = [int(x) for x in np.linspace(0, L512 - 1, nslices).round()]
+            if f512 is None:
+                f512 = inputs.smooth_coeffs(L512, L512, L512, 1.1, inputs.rng_for(SEED_512))
+            self.jobs = [(s, np.ascontiguousarray(f512[s]), steps) for s in self.slices]
+            self.fn = _oracle_worker_512
+            self.units = nslices * L512 * L512 * (1 + steps)
+            self.sample = ('%d of %d theta-slices of the 512^3 workload, each: Poisson solve + %d BDF1 heat steps '
+                           '(QZ Bartels-Stewart per slice, including its per-wavenumber QZ set-up), spread over %d '
+                           'single-threaded worker processes (solve time only)' % (nslices, L512, steps, self.procs))
+        else:
+            self.L = P
+            self.slices = [int(x) for x in np.linspace(0, P - 1, nslices).round()]
+            self.jobs = [([s], steps) for s in self.slices]
+            self.fn = _oracle_worker_128
+            self.units = nslices * M * N_Z * steps
+            self.sample = ('%d of %d theta-slices x %d BDF1 steps of the 128^3 heat problem (QZ Bartels-Stewart '
+                           'per slice), spread over %d single-threaded worker processes (solve time only)'
+                           % (nslices, P, steps, self.procs))
+        # the children read these when their BLAS loads (at import, before any worker code runs): one
+        # thread per process, so that the processes do not oversubscribe the cores
+        saved = {v: os.environ.get(v) for v in BLAS_THREAD_VARS}
+        for v in BLAS_THREAD_VARS:
+            os.environ[v] = '1'
+        try:
+            self.pool = mp.get_context('spawn').Pool(processes=self.procs)
+        finally:
+            for v, val in saved.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
+
+    def run(self):
+        """(unknowns*steps/s of the worker cores, busy seconds, outputs by slice)."""
+        res = self.pool.map(self.fn, self.jobs, chunksize=1)
+        out = {}
+        for _, d in res:
+            out.update(d)
+        busy = sum(t for t, _ in res) / self.procs
+        return self.units / busy, busy, out
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 # ----------------------------------------------------------------- clocks
@@ -163,12 +227,24 @@ def aggregate(t_local, units_local, dist=None, device=None):
     return float(t.item()), float(u.item())
 
 
-def hbm_line(wl, seconds_per_step):
+def traffic_of(wl):
+    """(DRAM bytes read + written per bench step of the dominant kernel, basis)
+    from the workload's ncu capture, or (None, why) when there is none or the
+    kernel source changed since the capture."""
+    if wl.TRAFFIC is None:
+        return None, 'no ncu capture for this workload'
+    nbytes, src = wl.TRAFFIC
+    if src != source_hash():
+        return None, 'stale: kernel source changed since the ncu capture (source %s, now %s)' % (src, source_hash())
+    return wl.traffic_scale(nbytes), wl.TRAFFIC_BASIS + ' (kernel source %s)' % src
+
+
+def hbm_line(traffic, seconds_per_step):
     """Where the dominant kernel sits against the HBM roofline: its DRAM
     traffic per bench step over the step time, against the measured copy
     bandwidth (MEASURED_PEAKS.json, else the 6.8 TB/s fallback) and the
     nominal 7.9 TB/s."""
-    if wl.traffic is None:
+    if traffic is None:
         return None
     peak, basis = 6800.0, 'of fallback'
     try:
@@ -176,26 +252,56 @@ def hbm_line(wl, seconds_per_step):
             peak, basis = float(json.load(fh)['hbm_gbs']), 'of measured'
     except (OSError, KeyError, ValueError):
         pass
-    gbs = wl.traffic / seconds_per_step / 1e9
+    gbs = traffic / seconds_per_step / 1e9
     return {'achieved_gbs': gbs, 'peak_gbs': peak, 'frac': gbs / peak, 'basis': basis,
-            'frac_of_nominal_7900': gbs / 7900.0}
+            'frac_of_nominal_7900': gbs / 7900.0,
+            'reason': 'not the binding roofline: the ADI kernels are FP64-ALU bound (all J iterations and time '
+                      'steps of an item run inside one launch with its work arrays on chip or in L2)'}
 
 
-def adi_flops_per_launch(plan, nsteps):
-    """Algorithmic FP64 flops of one fused heat launch (the library's count)."""
-    return plan.flops(1, nsteps)
+def fp64_probe(cyl, torch, dev, stream):
+    """FP64 FMA throughput of this GPU now (cyl_fp64_fma_probe: 2 x 152 CTAs of
+    512 threads, 8 independent chains per thread), timed with CUDA events on
+    the launching stream, with the SM clock sampled during the launches."""
+    blocks, threads, iters = 2 * SM_COUNT, 512, 20000
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        cyl.fp64_fma_probe(sink, blocks, threads, iters, stream.cuda_stream)
+    torch.cuda.synchronize()
+    clk = ClockSampler()
+    clk.start()
+    time.sleep(0.3)
+    best, flops = None, 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = cyl.fp64_fma_probe(sink, blocks, threads, iters, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    c = clk.stop()
+    tf = flops / (best * 1e-3) / 1e12
+    out = {'tflops': tf, 'sm_mhz': c['sm_mhz'], 'ms': best,
+           'fma_per_clk_per_sm': (tf * 1e12 / 2 / SM_COUNT / (c['sm_mhz'] * 1e6)) if c['sm_mhz'] else None}
+    return out
 
 
 # ----------------------------------------------------------------- workloads
 class Workload:
     """units: unknowns*steps per bench step; flops: algorithmic FP64 flops of
     the dominant kernel per bench step; launches: our kernel launches per step;
-    traffic: DRAM bytes (read + write) of one launch of the dominant kernel
-    from an ncu capture of this workload (profiles/), or None."""
+    TRAFFIC: (DRAM bytes read + written per bench step of the dominant kernel
+    from an ncu capture, short hash of the kernel sources it was taken on;
+    see source_hash), or None."""
     name = ''
     config = {}
-    traffic = None
-    traffic_basis = None
+    TRAFFIC = None
+    TRAFFIC_BASIS = ''
+    cpu = None                  # OracleSampler of this workload's CPU baseline, when it has one
+
+    def traffic_scale(self, nbytes):
+        return nbytes
 
     def extra(self, stream, reps):
         return {}
@@ -203,15 +309,19 @@ class Workload:
     def reset(self):
         pass
 
+    def accuracy(self):
+        return {}
+
     def e2e_bytes(self):
         return 0, 0
 
 
 class Heat128(Workload):
     name = 'heat128'
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch
-    # (49,261,312 + 1,183,488 bytes; profiles/adi_kernel_heat128.md)
-    TRAFFIC = 49261312 + 1183488
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch, taken before
+    # the kernel-source hash was recorded: reported as stale until captured again
+    TRAFFIC = (49261312 + 1183488, None)
+    TRAFFIC_BASIS = 'ncu capture of the bench launch'
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
         self.torch = torch
@@ -228,12 +338,29 @@ class Heat128(Workload):
         self.flops = self.plan.flops(1, nsteps)
         self.launches = 1
         self.kernel = 'adi_kernel'
-        self.traffic = self.TRAFFIC if nsteps == NSTEPS else None
-        self.traffic_basis = 'ncu capture of the bench launch' if self.traffic else None
+        if nsteps != NSTEPS:
+            self.TRAFFIC = None
         self.config = {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF1 steps, '
                                    '8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
-                       'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nsteps, 'adi_tol': TOL}
+                       'n_r': M, 'n_z': N_Z, 'n_theta': P, 'time_steps_per_bench_step': nsteps, 'adi_tol': TOL,
+                       'l2': 'flushed between timed steps (256 MB write)'}
         self.host = None
+        self.dev = dev
+
+    def accuracy(self):
+        """The 128^3 heat run from the CPU baseline's inputs, compared with the
+        oracle's output on the sampled slices."""
+        if self.cpu is None or self.cpu_out is None:
+            return {}
+        t = self.torch
+        X0c, gc = _host_inputs_coeffs(inputs.rng_for(SEED))
+        Tc = t.as_tensor(X0c, device=self.dev)
+        self.plan.heat_step(Tc, t.as_tensor(gc, device=self.dev), self.cpu.steps)
+        Tc = Tc.cpu().numpy()
+        sl = self.cpu.slices
+        ref = np.stack([self.cpu_out[s] for s in sl])
+        got = np.stack([Tc[s] for s in sl])
+        return {'max_rel_err_vs_oracle': float(np.abs(got - ref).max() / np.abs(ref).max())}
 
     def reset(self):
         self.T.copy_(self.T0)
@@ -315,35 +442,58 @@ class Poisson33(Workload):
 
 class Large512(Workload):
     name = 'large512'
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches
-    # (Poisson 102,546,660,096 + 88,557,331,456; 20 heat steps 1,747,276,132,864 + 1,472,403,574,784;
-    # profiles/adi_kernel_large512.md)
-    TRAFFIC = 102546660096 + 88557331456 + 1747276132864 + 1472403574784
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches (Poisson
+    # 102,546,660,096 + 88,557,331,456; 20 heat steps 1,747,276,132,864 + 1,472,403,574,784), taken
+    # before the kernel-source hash was recorded: reported as stale until captured again
+    TRAFFIC = (102546660096 + 88557331456 + 1747276132864 + 1472403574784, None)
+    TRAFFIC_BASIS = 'ncu capture of the bench step (two launches)'
 
-    def __init__(self, cyl, torch, dev, stream, nsteps):
-        m = n = p = 512
+    def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None):
+        m = n = p = L512
         self.torch, self.cyl = torch, cyl
         # ADI tolerance 1e-15: at 1e-14 the 20-step run ends at 1.7e-12 of the (refined) oracle, the
         # Zolotarev bound being optimistic for the non-normal 512-point pencils
-        self.plan = cyl.Plan(m, n, p, 0.1, 1e-4, TOL_512, poisson=True, heat=True, stream=stream.cuda_stream)
-        rng = inputs.rng_for(1002)
-        self.f = torch.as_tensor(inputs.smooth_coeffs(p, m, n, 1.1, rng), device=dev)
+        self.plan = cyl.Plan(m, n, p, ALPHA_512, DT_512, TOL_512, poisson=True, heat=True,
+                             stream=stream.cuda_stream)
+        if f_host is None:
+            f_host = inputs.smooth_coeffs(p, m, n, 1.1, inputs.rng_for(SEED_512))
+        self.f = torch.as_tensor(f_host, device=dev)
         self.T = torch.empty_like(self.f)
-        self.hsteps = 20
+        self.hsteps = HSTEPS_512
         self.units = m * n * p * (1 + self.hsteps)
         self.flops = self.plan.flops(0, 1) + self.plan.flops(1, self.hsteps)
         self.launches = 2
         self.kernel = 'adi_kernel'
-        self.traffic = self.TRAFFIC
-        self.traffic_basis = 'ncu capture of the bench step (two launches)'
         self.config = {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
                                    'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out',
-                       'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL_512}
+                       'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL_512,
+                       'time_steps_per_bench_step': 1 + self.hsteps,
+                       'l2': 'inputs larger than L2 (1.07 GB per field)'}
         self.host = None
 
     def step(self):
         self.plan.poisson(self.f, self.T, self.cyl.COEFFS)
         self.plan.heat_step(self.T, self.f, self.hsteps)
+
+    def accuracy(self):
+        """The last timed step's final state and a fresh Poisson solve, on the
+        sampled slices and coefficients of the oracle's stored 512^3 values."""
+        t = self.torch
+        ref = np.load(GOLD512)
+        sl = t.as_tensor(ref['slices'], device=self.T.device)
+        idx = t.as_tensor(ref['idx'], device=self.T.device)
+        pick = lambda X: X.index_select(0, sl).index_select(1, idx).index_select(2, idx).cpu().numpy()
+        h = pick(self.T)
+        u = t.empty_like(self.T)
+        self.plan.poisson(self.f, u, self.cyl.COEFFS)
+        u = pick(u)
+        del_u = float(np.abs(u - ref['poisson']).max() / np.abs(ref['poisson']).max())
+        del_h = float(np.abs(h - ref['heat']).max() / np.abs(ref['heat']).max())
+        return {'max_rel_err_vs_oracle': max(del_u, del_h),
+                'accuracy_detail': {'poisson': del_u, 'after_20_heat_steps': del_h,
+                                    'reference': 'oracle values on %d slices x %d x %d coefficients '
+                                                 '(tests/golden/large512_sampled.npz)'
+                                                 % (len(ref['slices']), len(ref['idx']), len(ref['idx']))}}
 
     def e2e_setup(self):
         t = self.torch
@@ -361,6 +511,15 @@ class Large512(Workload):
 
 class Batch256(Workload):
     name = 'batch256'
+    # DRAM bytes of one step of a 32-problem batch of 43,257,728 unknowns (949,844,224 read +
+    # 392,462,592 written), taken before the kernel-source hash was recorded; the traffic (T, g and
+    # the right sides per item and step) grows with unknowns x steps
+    TRAFFIC = (949844224 + 392462592, None)
+    TRAFFIC_BASIS = 'scaled from one ncu capture (32 problems, 1 step) by unknowns x steps'
+    TRAFFIC_UNITS = 43257728
+
+    def traffic_scale(self, nbytes):
+        return nbytes / self.TRAFFIC_UNITS * self.units
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
         self.torch, self.cyl, self.stream = torch, cyl, stream
@@ -378,11 +537,6 @@ class Batch256(Workload):
         self.tune_ms = self.bp.autotune(self.T, self.g, 1)
         self.units = self.bp.N * self.steps
         self.flops = self.bp.flops(self.steps)
-        # DRAM bytes per unknown and step of the batch kernel: 949,844,224 + 392,462,592 bytes for one
-        # step of a 32-problem batch of 43,257,728 unknowns (profiles/adi_batch_kernel_batch256.md); the
-        # traffic (T, g and the right sides per item and step) grows with unknowns x steps
-        self.traffic = (949844224 + 392462592) / 43257728 * self.units
-        self.traffic_basis = 'scaled from one ncu capture (32 problems, 1 step) by unknowns x steps'
         self.launches = 2
         self.kernel = 'adi_batch_kernel'
         thr, G, counts = self.bp.config()
@@ -511,7 +665,7 @@ class Heat128Bdf4(Heat128):
         start = min(b - 1, nsteps)
         self.flops = sum(self.plan.flops(o, 1) for o in range(1, start + 1)) + self.plan.flops(b, nsteps - start)
         self.launches = start + (1 if nsteps > start else 0) + (1 if (-nsteps) % b else 0)
-        self.traffic = None
+        self.TRAFFIC = None
         self.config = dict(self.config, workload='heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, %d BDF4 steps '
                            '(start-up through BDF 1-3), 8 Bessel x sine eigenmodes + smooth forcing' % nsteps,
                            bdf_order=b)
@@ -536,11 +690,14 @@ class Heat128Bdf4(Heat128):
         outh.copy_(self.H[0], non_blocking=True)
 
 
-WORKLOADS = {'heat128': Heat128, 'poisson33': Poisson33, 'large512': Large512, 'batch256': Batch256,
+WORKLOADS = {'large512': Large512, 'heat128': Heat128, 'poisson33': Poisson33, 'batch256': Batch256,
              'adjoint128': Adjoint128, 'heat128_bdf4': Heat128Bdf4}
 
 
 # ----------------------------------------------------------------- GPU leg
+CPU_LEGS = ('large512', 'heat128')      # workloads with an oracle CPU baseline on rank 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -551,32 +708,30 @@ def run_ours(args):
     torch.cuda.set_device(_local_rank())
     dev = torch.device('cuda', _local_rank())
 
-    # CPU baseline and accuracy sample first (spawned pool before heavy GPU use)
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.workload == 'heat128':
-        rate, wall, cores, sl, oracle_out = run_oracle_sample(args.cpu_slices, args.cpu_steps)
-        cpu = dict(value=rate, wall=wall, cores=cores, slices=sl, out=oracle_out)
+    # CPU baseline first (the pool is spawned; the sample runs before heavy GPU use)
+    cpu, cpu_res, f512 = None, None, None
+    if args.workload == 'large512':
+        f512 = inputs.smooth_coeffs(L512, L512, L512, 1.1, inputs.rng_for(SEED_512))
+    if rank == 0 and not args.no_cpu_baseline and args.workload in CPU_LEGS:
+        cpu = OracleSampler(args.workload, args.cpu_slices, args.cpu_steps, f512=f512)
+        cpu_res = cpu.run()
+        cpu.close()
 
     from paper_2206_04827_gb300 import cyl
     stream = torch.cuda.current_stream(dev)
-    wl = WORKLOADS[args.workload](cyl, torch, dev, stream, args.nsteps)
+    if args.workload == 'large512':
+        wl = Large512(cyl, torch, dev, stream, args.nsteps, f_host=f512)
+    else:
+        wl = WORKLOADS[args.workload](cyl, torch, dev, stream, args.nsteps)
+    f512 = None
+    wl.cpu, wl.cpu_out = cpu, (cpu_res[2] if cpu_res else None)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    probe = fp64_probe(cyl, torch, dev, stream)
 
     for _ in range(args.warmup):
         wl.reset()
         wl.step()
     torch.cuda.synchronize()
-
-    # accuracy: the 128^3 heat run compared with the oracle on the sampled slices
-    acc = None
-    if cpu is not None:
-        X0c, gc = _host_inputs_coeffs(inputs.rng_for(SEED))
-        Tc = torch.as_tensor(X0c, device=dev)
-        wl.plan.heat_step(Tc, torch.as_tensor(gc, device=dev), args.cpu_steps)
-        Tc = Tc.cpu().numpy()
-        ref = np.stack([cpu['out'][s] for s in cpu['slices']])
-        got = np.stack([Tc[s] for s in cpu['slices']])
-        acc = float(np.abs(got - ref).max() / np.abs(ref).max())
 
     if world > 1:
         dist.barrier()
@@ -602,6 +757,7 @@ def run_ours(args):
     clocks = clk.stop()
     t_local = sum(a.elapsed_time(b) * 1e-3 for a, b in evs)
     t_sum, units_all = aggregate(t_local, wl.units * args.steps, dist if world > 1 else None, dev)
+    acc = wl.accuracy()
 
     # end to end through the C ABI with pinned host buffers
     wl.e2e_setup()
@@ -622,30 +778,30 @@ def run_ours(args):
     peak_mhz = clocks['sm_max_mhz'] or 2070.0
     peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * peak_mhz * 1e6
     achieved = wl.flops / (t_sum / args.steps)
+    traffic, tbasis = traffic_of(wl)
     line = {
         'metric': METRIC, 'value': units_all / t_sum, 'unit': UNIT,
         'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
         'ms_per_step': 1e3 * t_sum / args.steps, 'higher_is_better': True, 'scaling': 'weak',
         'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': dict(wl.config, l2='flushed between timed steps (256 MB write)',
-                       parallelism='replicas' if world > 1 else 'single'),
+        'config': dict(wl.config, parallelism='replicas' if world > 1 else 'single'),
         'roofline': {'bound': 'alu', 'achieved': achieved / 1e12, 'peak': peak / 1e12, 'unit': 'TFLOP/s',
-                     'frac': achieved / peak, 'traffic': wl.traffic, 'traffic_basis': wl.traffic_basis,
-                     'peak_basis': '152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (of derived)',
-                     'kernel': wl.kernel, 'hbm': hbm_line(wl, t_sum / args.steps)},
+                     'frac': achieved / peak, 'traffic': traffic, 'traffic_basis': tbasis,
+                     'peak_basis': '152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock (of derived); '
+                                   'the live probe measures the FMA rate per clock',
+                     'fp64_probe': probe,
+                     'kernel': wl.kernel, 'hbm': hbm_line(traffic, t_sum / args.steps)},
         'e2e': {'value': world * wl.units * len(e2e) / sum(e2e), 'unit': UNIT,
                 'h2d_bytes_per_step': int(h2d), 'd2h_bytes_per_step': int(d2h)},
         'gpu_launches': wl.launches * args.steps,
         'clocks': {k: clocks[k] for k in ('sm_mhz', 'sm_max_mhz', 'reasons')},
         'wall_s': wall,
+        'kernel_source': source_hash(),
     }
     if cpu is not None:
-        line['cpu_baseline'] = {'value': cpu['value'], 'unit': UNIT, 'cores': cpu['cores'], 'kind': 'oracle',
-                                'sample': '%d of %d theta-slices x %d BDF1 steps of the 128^3 heat problem '
-                                          '(QZ Bartels-Stewart per slice; slices spread over %d single-threaded '
-                                          'worker processes, solve time only)'
-                                          % (len(cpu['slices']), P, args.cpu_steps, cpu['cores'])}
-        line['max_rel_err_vs_oracle'] = acc
+        line['cpu_baseline'] = {'value': cpu_res[0], 'unit': UNIT, 'cores': cpu.procs, 'kind': 'oracle',
+                                'sample': cpu.sample}
+    line.update(acc)
     line.update(wl.extra(stream, 20))
     if isinstance(wl, Batch256):
         plain = wl.plain_rate()
@@ -662,22 +818,26 @@ def run_reference(args):
     rank = int(os.environ.get('RANK', '0'))
     if rank != 0:
         return
+    wlname = args.workload if args.workload in CPU_LEGS else 'large512'
+    smp = OracleSampler(wlname, args.cpu_slices, args.cpu_steps)
     for _ in range(args.warmup):
-        run_oracle_sample(args.cpu_slices, 1)
-    walls, cores = [], 1
+        smp.pool.map(smp.fn, smp.jobs[:1], chunksize=1)     # imports and first touch in one worker
+    walls = []
     for _ in range(args.steps):
-        _, wall, cores, _, _ = run_oracle_sample(args.cpu_slices, args.cpu_steps)
-        walls.append(wall)
-    value = len(walls) * args.cpu_slices * M * N_Z * args.cpu_steps / sum(walls)
-    sample = ('%d of %d theta-slices x %d BDF1 steps of the 128^3 heat problem per bench step, spread over %d '
-              'single-threaded worker processes (solve time only)' % (args.cpu_slices, P, args.cpu_steps, cores))
+        _, busy, _ = smp.run()
+        walls.append(busy)
+    smp.close()
+    value = len(walls) * smp.units / sum(walls)
+    cfg = {'large512': {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
+                                    'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out',
+                        'n_r': L512, 'n_z': L512, 'n_theta': L512, 'adi_tol': TOL_512},
+           'heat128': {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, BDF1, smooth forcing',
+                       'n_r': M, 'n_z': N_Z, 'n_theta': P}}[wlname]
     print(json.dumps({
         'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': 0, 'steps': args.steps,
         'warmup': args.warmup, 'ms_per_step': 1e3 * sum(walls) / len(walls), 'higher_is_better': True,
-        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-        'config': {'workload': 'heat 128^3 (n_r=n_z=n_theta=128), alpha=1, dt=1e-3, BDF1, smooth forcing',
-                   'n_r': M, 'n_z': N_Z, 'n_theta': P},
-        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': cores, 'kind': 'oracle', 'sample': sample},
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic', 'config': cfg,
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': smp.procs, 'kind': 'oracle', 'sample': smp.sample},
         'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
     }), flush=True)
 
@@ -688,9 +848,11 @@ def main():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--workload', default='heat128', choices=sorted(WORKLOADS))
-    ap.add_argument('--cpu-slices', type=int, default=16)
-    ap.add_argument('--cpu-steps', type=int, default=30)
+    ap.add_argument('--workload', default='large512', choices=sorted(WORKLOADS))
+    ap.add_argument('--cpu-slices', type=int, default=16,
+                    help='theta-slices of the CPU oracle sample (one per worker process)')
+    ap.add_argument('--cpu-steps', type=int, default=None,
+                    help='heat steps per sampled slice (default: 2 after the Poisson solve at 512^3, 30 at 128^3)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--batch-problems', type=int, default=256,
                     help='problems of the batch256 workload (256 = the workload; fewer only for profiling)')
@@ -699,6 +861,8 @@ def main():
     args = ap.parse_args()
     global BATCH_PROBLEMS
     BATCH_PROBLEMS = args.batch_problems
+    if args.cpu_steps is None:
+        args.cpu_steps = 30 if args.workload == 'heat128' else 2
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == 'reference':

@@ -362,10 +362,9 @@ cyl_status cyl_sync(cyl_plan_t plan);
  * cyl_vals2coeffs_noalloc -- the values -> coefficients transform of
  * cyl_vals2coeffs without a plan and without any allocation.  The paper has
  * no counterpart; this entry point exists for callers that cannot allocate
- * device memory: code running while a CUDA graph is captured (cudaMalloc is
- * not allowed there), hosts whose own pool owns all device memory, and
- * loops that must never enter an allocator.  cyl_plan allocates, so such
- * callers cannot use the planned entry points.
+ * device memory: hosts whose own pool owns all device memory and forbids
+ * other allocations, and loops that must never enter an allocator.
+ * cyl_plan allocates, so such callers cannot use the planned entry points.
  *
  *   n_r, n_z     >= 2; n_theta even and >= 2.
  *   vals, coeffs caller-owned device arrays of n_r*n_z*n_theta float64
@@ -376,13 +375,16 @@ cyl_status cyl_sync(cyl_plan_t plan);
  * (64 MiB) that every device context loading the library holds until the
  * process exits.  A call needs 2 N + n_r^2 + n_z^2 + n_theta^2 doubles of it
  * (N = n_r n_z n_theta; e.g. 160^3 fits, 170^3 does not); larger problems
- * return CYL_EINVAL and launch nothing.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call uses
- * the same array and fully rewrites what it reads, so nothing needs clearing
- * between calls, but calls whose kernels overlap on the GPU (different
- * streams, or different host threads) race on the array and give wrong
- * results: serialise them.  Calls no cudaMalloc or cudaFree.
+ * return CYL_EINVAL and launch nothing.  The first call in each CUDA context
+ * looks up the array's device address (cudaGetSymbolAddress, with the device
+ * current) and caches it under the context's unique ID; after
+ * cudaDeviceReset the device's new context gets its own lookup on the next
+ * call.  Every call uses the same array and fully rewrites what it reads, so
+ * nothing needs clearing between calls, but calls whose kernels overlap on
+ * the GPU (different streams, or different host threads) race on the array
+ * and give wrong results: serialise them.  A launch error left pending by the
+ * caller's earlier work is returned as CYL_ECUDA before anything is
+ * launched.  Calls no cudaMalloc or cudaFree.
  */
 #define CYL_NOALLOC_SCRATCH_DOUBLES (1 << 23)
 cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, const double *vals, double *coeffs,
@@ -390,6 +392,24 @@ cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, const double *
 
 /* Human-readable name of a status code (static string). */
 const char *cyl_status_string(cyl_status s);
+
+/*
+ * cyl_fp64_fma_probe -- measurement of the machine, not of the method (the
+ * paper has no counterpart): the FP64 fused multiply-add throughput that the
+ * FP64 roofline of the ADI kernels divides by.  Launches blocks x threads
+ * threads on `stream`, each running 8 independent FMA chains for `iters`
+ * iterations, and stores in *flops (host) the launch's FP64 flops (2 per
+ * FMA).  The caller times the launch (CUDA events on `stream`) and divides.
+ *
+ *   blocks >= 1; threads a multiple of 32 in 32..1024; iters >= 1.
+ *   sink   device array of blocks*threads float64; never written for the
+ *          probe's arguments, it only keeps the chains from being removed.
+ *
+ * CYL_EINVAL for bad arguments, CYL_ECUDA when the launch fails.  Allocates
+ * nothing.
+ */
+cyl_status cyl_fp64_fma_probe(int blocks, int threads, long long iters, double *sink, double *flops,
+                              void *stream);
 
 /* ---------------------------------------------------------------------------
  * Host-side introspection (no device access; valid on CYL_HOST_ONLY plans).

@@ -2,16 +2,18 @@
 //
 // cyl_vals2coeffs needs a plan, and building a plan allocates device memory
 // (operator tables, factors, two N-element scratch arrays).  Some callers
-// cannot allocate at all: code that runs while a CUDA graph is being captured
-// (cudaMalloc is not allowed during capture), hosts that hand every byte of
-// device memory to their own pool and forbid other allocations, and
-// latency-critical loops that must never enter the allocator.  For them this
-// file provides cyl_vals2coeffs_noalloc: the same three axis transforms, with
-// the scratch (two intermediate arrays and the three transform matrices) taken
-// from a fixed array in the library's own device image.
+// cannot allocate at all: hosts that hand every byte of device memory to
+// their own pool and forbid other allocations, and latency-critical loops
+// that must never enter the allocator.  For them this file provides
+// cyl_vals2coeffs_noalloc: the same three axis transforms, with the scratch
+// (two intermediate arrays and the three transform matrices) taken from a
+// fixed array in the library's own device image.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "../../include/cyl.h"
 #include "kernels.cuh"
@@ -22,26 +24,60 @@ namespace {
 // device context that loads this library, held until the process exits.
 __device__ __align__(256) double g_noalloc_scratch[CYL_NOALLOC_SCRATCH_DOUBLES];
 
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
+// In host code the symbol name is only a host-side stand-in, so the array's
+// device address is looked up (cudaGetSymbolAddress, with the device
+// current) and cached.  The cache is keyed by the CUDA context's unique ID,
+// not by the device number: after cudaDeviceReset the device gets a new
+// primary context, in which the array may sit at another address, and the
+// lookup is then made again.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 std::mutex g_scratch_mu;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::vector<std::pair<unsigned long long, double *>> g_scratch_by_ctx;
 
-// Device address of the scratch array for the current device.  In host code
-// the symbol name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-cudaError_t scratch_for_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+// Unique ID of the calling thread's current context (0 when none is current).
+cudaError_t current_context_id(unsigned long long *id) {
+  *id = 0;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double *>(p);
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorNotSupported;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = g_scratch_ptr[dev];
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (!ctx) return cudaSuccess;
+  if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of the scratch array in the current context.
+cudaError_t scratch_for_current_context(double **out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  unsigned long long id = 0;
+  cudaError_t e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  if (id != 0)
+    for (const auto &kv : g_scratch_by_ctx)
+      if (kv.first == id) {
+        *out = kv.second;
+        return cudaSuccess;
+      }
+  // first call in this context (or no context yet: the lookup creates the
+  // device's primary context and makes it current)
+  void *p = nullptr;
+  if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+  if (id == 0 && ((e = current_context_id(&id)) != cudaSuccess || id == 0))
+    return e != cudaSuccess ? e : cudaErrorDeviceUninitialized;
+  g_scratch_by_ctx.emplace_back(id, static_cast<double *>(p));
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 
@@ -98,8 +134,11 @@ extern "C" cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, con
   const long long m = n_r, n = n_z, p = n_theta, N = m * n * p;
   const long long need = 2 * N + m * m + n * n + p * p;
   if (need > (long long)CYL_NOALLOC_SCRATCH_DOUBLES) return CYL_EINVAL;
+  // a launch error left pending by the caller's earlier work would otherwise
+  // be read back below as a failure of this call: report it before launching
+  if (cudaPeekAtLastError() != cudaSuccess) return CYL_ECUDA;
   double *base = nullptr;
-  cudaError_t e = scratch_for_current_device(&base);
+  cudaError_t e = scratch_for_current_context(&base);
   if (e != cudaSuccess) return CYL_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double *buf0 = base, *buf1 = base + N;

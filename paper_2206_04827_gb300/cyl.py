@@ -73,6 +73,7 @@ _sig = {
     'cyl_batch_autotune': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
     'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+    'cyl_fp64_fma_probe': (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _c_double_p, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -355,6 +356,15 @@ def plan_flops(handle, which, nsteps, transposed):
     f = ctypes.c_double()
     _check(_lib.cyl_plan_flops(handle, int(which), int(nsteps), int(bool(transposed)), ctypes.byref(f)),
            'cyl_plan_flops')
+    return f.value
+
+
+def fp64_fma_probe(sink, blocks, threads, iters, stream):
+    """Launch the FP64 FMA-throughput probe (include/cyl.h: cyl_fp64_fma_probe) on
+    `stream`; returns the launch's FP64 flops.  The caller times it."""
+    f = ctypes.c_double()
+    _check(_lib.cyl_fp64_fma_probe(int(blocks), int(threads), int(iters), _ptr(sink, 'sink', blocks * threads),
+                                   ctypes.byref(f), _vp(stream)), 'cyl_fp64_fma_probe')
     return f.value
 
 

@@ -1,9 +1,10 @@
 """The allocation-free transform entry point (cyl_vals2coeffs_noalloc) called
 through the C ABI must give what the planned transform (cyl_vals2coeffs)
 gives, on consecutive calls that share its fixed scratch array.  It serves
-callers that cannot allocate device memory (graph capture, foreign memory
-pools), so it is checked here against the planned path, within the
-transform tolerance used by the other GPU tests."""
+callers that cannot allocate device memory (hosts whose own pool owns all
+device memory, loops that must never enter an allocator), so it is checked
+here against the planned path, within the transform tolerance used by the
+other GPU tests, also when the input and output arrays are the same."""
 import ctypes
 
 import numpy as np
@@ -45,6 +46,18 @@ def test_noalloc_transform_matches_planned_on_consecutive_calls(cyl):
         w, g = want.cpu().numpy(), got.cpu().numpy()
         assert np.abs(g - w).max() / np.abs(w).max() <= TOL_XFORM
         plan.close()
+
+
+def test_noalloc_in_place(cyl):
+    m, n, p = 33, 29, 16
+    vals = torch.as_tensor(np.random.default_rng(4).standard_normal((p, m, n)), device='cuda')
+    plan = cyl.Plan(m, n, p)
+    want = plan.vals2coeffs(vals, torch.empty_like(vals)).cpu().numpy()
+    t = vals.clone()
+    assert _noalloc(cyl, m, n, p, t, t) == cyl.OK
+    torch.cuda.synchronize()
+    assert np.abs(t.cpu().numpy() - want).max() / np.abs(want).max() <= TOL_XFORM
+    plan.close()
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(cyl):
