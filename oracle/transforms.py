@@ -14,17 +14,47 @@ Im c_w for w = 1 .. p/2-1; slice p-1 holds c_{-p/2}, which is real on the
 doubled grid.  Negative wavenumbers follow from c_{-w} = conj(c_w).
 """
 import numpy as np
-from numpy.polynomial import chebyshev as npcheb
 
 from . import grid
+
+
+def _cos_pi_ratio(r, d):
+    """cos(pi r / d) for integer arrays r, d > 0: r is reduced exactly modulo
+    2d in integers and folded to an angle in [0, pi/2] before the cosine, so
+    large degrees or wavenumbers add no rounding of their own."""
+    r = np.mod(np.asarray(r, dtype=np.int64), 2 * d)
+    r = np.where(r > d, 2 * d - r, r)                 # cos is even about pi
+    sign = np.where(2 * r > d, -1.0, 1.0)             # cos(pi - t) = -cos(t)
+    r = np.where(2 * r > d, d - r, r)
+    return sign * np.cos(np.pi * r / d)
+
+
+def _cheb_at_grid(m):
+    """T[a, j] = T_j(x_a) on the grid of Definition "grid", from the defining
+    identity T_j(cos t) = cos(j t) with x_a = cos((m-1-a) pi / (m-1))."""
+    N = m - 1
+    a = np.arange(m, dtype=np.int64)[:, None]
+    j = np.arange(m, dtype=np.int64)[None, :]
+    return _cos_pi_ratio(j * (N - a), N)
+
+
+def _fourier_at_grid(p, sign):
+    """E[w, l] = exp(sign i w theta_l) for w = l' - p/2 (Section 2, CCF
+    polynomial) and theta_l = (2l - p) pi / p (Definition "grid"): the phase
+    w (2l - p) pi / p is reduced exactly in integers."""
+    w = grid.wavenumbers(p).astype(np.int64)[:, None]
+    l = np.arange(p, dtype=np.int64)[None, :]
+    r = w * (2 * l - p)                              # phase = pi r / p
+    c = _cos_pi_ratio(r, p)
+    s = _cos_pi_ratio(2 * r - p, 2 * p)            # sin(pi r / p) = cos(pi (2r - p) / (2p))
+    return c + sign * 1j * s
 
 
 def _cheb_forward_matrix(m):
     """DCT-I of Section 2 as a matrix: c_j = (2/(m-1)) w_j sum_a w_a f_a T_j(x_a),
     w = 1/2 at both ends, else 1 (discrete orthogonality of T_j at the
     Chebyshev extreme points)."""
-    x = grid.cheb_points(m)
-    V = npcheb.chebvander(x, m - 1)          # V[a, j] = T_j(x_a)
+    V = _cheb_at_grid(m)                     # V[a, j] = T_j(x_a)
     w = np.ones(m)
     w[0] = w[-1] = 0.5
     return (2.0 / (m - 1)) * (w[:, None] * (V * w[:, None]).T)
@@ -32,7 +62,7 @@ def _cheb_forward_matrix(m):
 
 def _cheb_inverse_matrix(m):
     """Evaluation of a T-series at the grid: f_a = sum_j c_j T_j(x_a)."""
-    return npcheb.chebvander(grid.cheb_points(m), m - 1)
+    return _cheb_at_grid(m)
 
 
 def vals2coeffs_complex(f):
@@ -44,9 +74,7 @@ def vals2coeffs_complex(f):
     Wz = _cheb_forward_matrix(n)
     g = np.einsum('ja,lab->ljb', Wr, f)          # DCT-I along r
     g = np.einsum('kb,ljb->ljk', Wz, g)          # DCT-I along z
-    th = grid.theta_points(p)
-    w = grid.wavenumbers(p)
-    E = np.exp(-1j * np.outer(w, th)) / p        # c_w = (1/p) sum_l f_l e^{-i w theta_l}
+    E = _fourier_at_grid(p, -1) / p              # c_w = (1/p) sum_l f_l e^{-i w theta_l}
     return np.einsum('wl,ljk->wjk', E, g)
 
 
@@ -55,9 +83,7 @@ def coeffs2vals_complex(C):
     p, m, n = C.shape
     Vr = _cheb_inverse_matrix(m)
     Vz = _cheb_inverse_matrix(n)
-    th = grid.theta_points(p)
-    w = grid.wavenumbers(p)
-    E = np.exp(1j * np.outer(th, w))             # E[l, w] = e^{i w theta_l}
+    E = _fourier_at_grid(p, +1).T                # E[l, w] = e^{i w theta_l}
     g = np.einsum('lw,wjk->ljk', E, C)
     g = np.einsum('aj,ljk->lak', Vr, g)
     return np.einsum('bk,lak->lab', Vz, g)

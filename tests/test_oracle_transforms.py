@@ -88,3 +88,27 @@ def test_bessel_generating_function():
         assert np.allclose(H[s, :, 0] @ T, special.iv(k, r), atol=1e-14)      # Re c_k
         if k > 0:
             assert np.abs(H[s + 1, :, 0] @ T).max() < 1e-14                    # Im c_k = 0
+
+
+def test_transform_matrices_accurate_at_high_degree():
+    """At 512 points per axis the oracle's DCT-I entries T_j(x_a) and Fourier
+    factors exp(-i w theta_l) agree with 40-digit evaluations (mpmath's own
+    Chebyshev polynomials and exponential), entry by entry: a three-term
+    recurrence or a floating-point phase w * theta_l drifts by ~1e-14 there,
+    which would exceed the transforms' 1e-13 bar after summation."""
+    mp = pytest.importorskip('mpmath')
+    mp.mp.dps = 40
+    L = 512
+    V = tr._cheb_inverse_matrix(L)
+    rng = np.random.default_rng(11)
+    for a, j in [(0, 511), (1, 255), (100, 300), (255, 256), (511, 511)] + \
+            [tuple(x) for x in rng.integers(0, L, size=(20, 2))]:
+        x = mp.cos(mp.pi * (L - 1 - a) / (L - 1))
+        assert abs(V[a, j] - float(mp.chebyt(int(j), x))) <= 4e-16
+    p = 512
+    E = tr._fourier_at_grid(p, -1)
+    w = grid.wavenumbers(p)
+    for wi, l in [(0, 511), (511, 3), (300, 300), (257, 100)] + [tuple(x) for x in rng.integers(0, p, size=(20, 2))]:
+        th = mp.mpf(2 * int(l) - p) * mp.pi / p
+        want = mp.exp(-1j * int(w[wi]) * th)
+        assert abs(E[wi, l] - complex(want)) <= 4e-16
