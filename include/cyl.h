@@ -75,6 +75,13 @@ typedef enum {
 #define CYL_PLAIN_SWEEPS 128u
 /* build the horizontal (disk) Poisson tables for cyl_disk_poisson */
 #define CYL_WITH_DISK    256u
+/* cluster mode on any grid (for tests).  Without the flag a plan uses it
+ * where one work item's iterate does not fit an SM's shared memory (about
+ * 220 points per axis and more): the CTAs of a thread-block cluster then
+ * share each item through its global work area, each with at most 128
+ * chains per sweep, solved as twisted two-thread chains.  CYL_FORCE_GLOBAL
+ * or CYL_PLAIN_SWEEPS turn cluster mode off. */
+#define CYL_FORCE_CLUSTER 512u
 
 /* space selector of cyl_poisson */
 #define CYL_VALUES 0
@@ -87,13 +94,14 @@ typedef enum {
  * Poisson analogue; Algorithm 1 (ADI); the shift choice below Algorithm 1
  * (Zolotarev-type shifts from K(k), dn and a Moebius map).
  *
- *   n_r, n_z   >= 4;  n_theta even and >= 2 (the doubled grid needs theta + pi).
+ *   n_r, n_z   4 .. 4096;  n_theta even, 2 .. 4096 (the doubled grid needs theta + pi).
  *   alpha, dt  > 0 when CYL_WITH_HEAT is set (diffusivity; BDF1 step kappa = dt).
  *   adi_tol    in (0, 1e-2]: target relative accuracy of the Zolotarev bound;
  *              the iteration count per mode is J = ceil(log(16 gamma) log(4/tol) / pi^2).
  *   flags      CYL_WITH_POISSON and/or CYL_WITH_HEAT, optionally
  *              CYL_BOTH_PARITIES, CYL_HOST_ONLY, CYL_FORCE_GLOBAL, CYL_WITH_BC,
- *              CYL_PLAIN_SWEEPS; CYL_WITH_DISK (alone or with the others).
+ *              CYL_PLAIN_SWEEPS, CYL_FORCE_CLUSTER; CYL_WITH_DISK (alone or
+ *              with the others).
  *   stream     cudaStream_t on which every device call of this plan runs
  *              (NULL = legacy default stream).  Ignored with CYL_HOST_ONLY.
  *
@@ -389,6 +397,21 @@ cyl_status cyl_sync(cyl_plan_t plan);
 #define CYL_NOALLOC_SCRATCH_DOUBLES (1 << 23)
 cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, const double *vals, double *coeffs,
                                    void *stream);
+
+/*
+ * cyl_xform_table -- host copy of the table block of one chirp-z line
+ * transform (Section 2: the DCT-I in r and z, the DFT in theta), as the
+ * plans build it.  kind: 0 = DCT-I forward, 1 = DCT-I inverse (L = number of
+ * Chebyshev points, 2..4096), 2 = DFT forward to half-complex, 3 = DFT
+ * inverse (L = n_theta, even, 2..4096).  info (11 ints, host): FFT length
+ * P, log2 P, input count A, output count B, first input index, first output
+ * index, offsets (doubles) of the pre-multipliers (A complex), the
+ * post-multipliers (B complex), the bit-reversed kernel spectrum scaled by
+ * 1/P (P complex), the FFT twiddles exp(-2 pi i k / P), k < P/2 (P/2
+ * complex), and the block's total length.  table: host array of that length,
+ * or NULL to query.  No device access.  CYL_EINVAL for bad arguments.
+ */
+cyl_status cyl_xform_table(int kind, int L, int *info, double *table);
 
 /* Human-readable name of a status code (static string). */
 const char *cyl_status_string(cyl_status s);

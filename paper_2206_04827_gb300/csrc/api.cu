@@ -29,10 +29,15 @@ struct cyl_plan_s {
   size_t smem[cyl::kNumKinds] = {};
   int use_smem[cyl::kNumKinds] = {1, 1, 1, 1, 1};
   int twist_half[cyl::kNumKinds] = {};   // > 0: the kind's tables hold twisted solves
+  int cluster = 0;                        // > 1: CTAs per item of the cluster-mode ADI launch
   int ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
   long long gwork_per_item = 0;
   double *d_gwork = nullptr;
-  double *d_W[6] = {};          // Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i
+  // chirp-z transform tables (csrc/xform.cu): z forward / inverse, r forward / inverse, theta forward / inverse
+  cyl::XformDesc xd[6];
+  long long xoff[6] = {};
+  double *d_xtab = nullptr;
+  int sms = 152;
   double *d_tmp[3] = {};        // N-element scratch arrays
   // batch plans (cyl_plan_batch): several problems, two persistent launch classes
   bool is_batch = false;
@@ -94,7 +99,7 @@ void free_device(cyl_plan_s *P) {
   cudaFree(P->d_fac);
   for (auto &p : P->d_items) cudaFree(p);
   cudaFree(P->d_gwork);
-  for (auto &p : P->d_W) cudaFree(p);
+  cudaFree(P->d_xtab);
   for (auto &p : P->d_tmp) cudaFree(p);
   cudaFree(P->d_err);
   cudaFree(P->d_apart);
@@ -109,26 +114,29 @@ cyl_status from_cuda(cudaError_t e) {
   return CYL_ECUDA;
 }
 
+// Section 2: DCT-I along z, then r, then the DFT along theta (chirp-z line transforms).
 cyl_status vals2coeffs_impl(cyl_plan_s *P, const double *vals, double *coeffs) {
   const HostPlan &h = P->hp;
   const long long m = h.m, n = h.n, p = h.p;
+  const double *T = P->d_xtab;
   cudaError_t e;
-  if ((e = cyl::launch_axis_matvec(vals, P->d_tmp[0], P->d_W[2], p * m, (int)n, 1, P->st)) != cudaSuccess)
+  if ((e = cyl::launch_xform(vals, P->d_tmp[0], T + P->xoff[0], P->xd[0], p * m, 1, P->sms, P->st)) != cudaSuccess)
     return from_cuda(e);
-  if ((e = cyl::launch_axis_matvec(P->d_tmp[0], P->d_tmp[1], P->d_W[0], p, (int)m, n, P->st)) != cudaSuccess)
+  if ((e = cyl::launch_xform(P->d_tmp[0], P->d_tmp[1], T + P->xoff[2], P->xd[2], p, n, P->sms, P->st)) != cudaSuccess)
     return from_cuda(e);
-  return from_cuda(cyl::launch_axis_matvec(P->d_tmp[1], coeffs, P->d_W[4], 1, (int)p, m * n, P->st));
+  return from_cuda(cyl::launch_xform(P->d_tmp[1], coeffs, T + P->xoff[4], P->xd[4], 1, m * n, P->sms, P->st));
 }
 
 cyl_status coeffs2vals_impl(cyl_plan_s *P, const double *coeffs, double *vals) {
   const HostPlan &h = P->hp;
   const long long m = h.m, n = h.n, p = h.p;
+  const double *T = P->d_xtab;
   cudaError_t e;
-  if ((e = cyl::launch_axis_matvec(coeffs, P->d_tmp[0], P->d_W[5], 1, (int)p, m * n, P->st)) != cudaSuccess)
+  if ((e = cyl::launch_xform(coeffs, P->d_tmp[0], T + P->xoff[5], P->xd[5], 1, m * n, P->sms, P->st)) != cudaSuccess)
     return from_cuda(e);
-  if ((e = cyl::launch_axis_matvec(P->d_tmp[0], P->d_tmp[1], P->d_W[1], p, (int)m, n, P->st)) != cudaSuccess)
+  if ((e = cyl::launch_xform(P->d_tmp[0], P->d_tmp[1], T + P->xoff[3], P->xd[3], p, n, P->sms, P->st)) != cudaSuccess)
     return from_cuda(e);
-  return from_cuda(cyl::launch_axis_matvec(P->d_tmp[1], vals, P->d_W[3], p * m, (int)n, 1, P->st));
+  return from_cuda(cyl::launch_xform(P->d_tmp[1], vals, T + P->xoff[1], P->xd[1], p * m, 1, P->sms, P->st));
 }
 
 cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
@@ -149,6 +157,7 @@ cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
   a.maxNz = P->maxNz;
   a.err = P->d_err;
   a.twist_half = P->twist_half[kind];
+  a.cluster = P->cluster;
   a.ckpt_every = 1;
   a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
   a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
@@ -170,8 +179,12 @@ cyl_status prepare_lift(cyl_plan_s *P, int kind, const double *bc) {
   // step operator of BDF b (kind b >= 1): c0 = 1, c1 = kappa^(b) alpha; Poisson: c0 = 0, c1 = 1
   const double c0 = kind >= 1 ? 1.0 : 0.0;
   const double c1 = kind >= 1 ? P->hp.alpha * P->hp.dt * cyl::bdf_kappa(kind) : 1.0;
-  return from_cuda(cyl::launch_lift(a, bc, P->d_corr, P->d_lift, P->d_corr, c0, c1, P->d_W[4], P->d_W[0],
-                                    P->d_W[2], P->d_tmp[0], P->d_tmp[1], std::min(P->threads[kind], 256), P->st));
+  // W's grid values go to d_corr (free until the correction overwrites it), its coefficients to d_lift
+  cudaError_t e2 = cyl::launch_lift_values(bc, P->d_corr, P->hp.p, P->hp.m, P->hp.n, P->st);
+  if (e2 != cudaSuccess) return from_cuda(e2);
+  cyl_status s = vals2coeffs_impl(P, P->d_corr, P->d_lift);
+  if (s != CYL_OK) return s;
+  return from_cuda(cyl::launch_lift_correction(a, P->d_lift, P->d_corr, c0, c1, std::min(P->threads[kind], 256), P->st));
 }
 
 cyl::AdiArgs step_args(cyl_plan_s *P, int kind, const double *Xin, double *Xout, const double *G, double kappa,
@@ -365,19 +378,34 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   if (!plan) return CYL_EINVAL;
   *plan = nullptr;
   if (n_r < 4 || n_z < 4 || n_theta < 2 || (n_theta & 1)) return CYL_EINVAL;
+  if (n_r > 4096 || n_z > 4096 || n_theta > 4096) return CYL_EINVAL;   // transform FFT length <= 8192
   if (!(adi_tol > 0.0) || adi_tol > 1e-2) return CYL_EINVAL;
   if (!(flags & (CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_WITH_DISK))) return CYL_EINVAL;
   if (flags & ~(unsigned)(CYL_WITH_POISSON | CYL_WITH_HEAT | CYL_BOTH_PARITIES | CYL_HOST_ONLY | CYL_FORCE_GLOBAL |
-                          CYL_TEST_NO_TMA | CYL_WITH_BC | CYL_PLAIN_SWEEPS | CYL_WITH_DISK))
+                          CYL_TEST_NO_TMA | CYL_WITH_BC | CYL_PLAIN_SWEEPS | CYL_WITH_DISK | CYL_FORCE_CLUSTER))
     return CYL_EINVAL;
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if (bdf_order < 1 || bdf_order > cyl::kMaxBdf) return CYL_EINVAL;
   if ((long long)n_r * n_z * n_theta > (1LL << 40)) return CYL_EINVAL;
+  // Cluster mode where one item's iterate S would not fit shared memory (its sizes follow from the
+  // grid: class rows (n_r + 1) / 2, class columns per slice (n_z + 1) / 2, two slices per item when
+  // n_theta >= 4): C CTAs per item, each with at most kTwistMaxChains chains per sweep.
+  int cluster = 0;
+  {
+    const int maxM = std::max(0, (n_r - 1) / 2), maxNz = std::max(0, (n_z - 1) / 2);
+    const int rows = (n_r + 1) / 2, nsl = n_theta >= 4 ? 2 : 1;
+    const int ld = (nsl * ((n_z + 1) / 2)) | 1;
+    const bool s_fits = cyl::adi_smem_bytes(ld, rows, maxM, maxNz, 1, 0) <= kSmemLimit;
+    const int chains = nsl * std::max(maxM, maxNz);
+    const int C = std::max(2, (chains + cyl::kTwistMaxChains - 1) / cyl::kTwistMaxChains);
+    if (!(flags & (CYL_FORCE_GLOBAL | CYL_PLAIN_SWEEPS)) && ((flags & CYL_FORCE_CLUSTER) || !s_fits) && C <= 8)
+      cluster = C;
+  }
   cyl_plan_s *P = new (std::nothrow) cyl_plan_s();
   if (!P) return CYL_ENOMEM;
   try {
     std::string err = cyl::build_host_plan(P->hp, n_r, n_z, n_theta, alpha, dt, adi_tol, flags, bdf_order,
-                                           !(flags & CYL_PLAIN_SWEEPS));
+                                           cluster ? 3 : !(flags & CYL_PLAIN_SWEEPS));
     if (!err.empty()) {
       delete P;
       return CYL_EINVAL;
@@ -420,7 +448,17 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
     }
     P->use_smem[kind] = level;
     P->smem[kind] = cyl::adi_smem_bytes(P->ld, P->smem_rows, P->maxM, P->maxNz, level, th);
+    if (cluster) {
+      // 256 threads (128 chains x 2 sides) per CTA, work arrays in global memory; at least 120 KB of
+      // shared memory keeps one CTA per SM, so that only (SMs / cluster) items are live in L2
+      P->threads[kind] = 2 * cyl::kTwistMaxChains;
+      P->twist_half[kind] = cyl::kTwistMaxChains;
+      P->use_smem[kind] = 0;
+      P->smem[kind] = std::max<size_t>(cyl::adi_cluster_smem_bytes(P->maxM, P->maxNz, cyl::kTwistMaxChains),
+                                       120 * 1024);
+    }
   }
+  P->cluster = cluster;
   for (int kind = 0; kind < cyl::kNumKinds; ++kind)
     if (P->threads[kind] > 512) {
       delete P;
@@ -436,8 +474,19 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
     P->nitems[kind] = (int)h.kind[kind].items.size();
     e = upload(&P->d_items[kind], h.kind[kind].items.data(), h.kind[kind].items.size());
   }
-  const std::vector<double> *Ws[6] = {&h.Wr_f, &h.Wr_i, &h.Wz_f, &h.Wz_i, &h.Wt_f, &h.Wt_i};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = upload(&P->d_W[i], Ws[i]->data(), Ws[i]->size());
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e == cudaSuccess) {
+    // transform tables: z forward / inverse (DCT-I, n points), r (m points), theta (DFT, p points)
+    std::vector<double> xt;
+    const int kinds[6] = {0, 1, 0, 1, 2, 3}, lens[6] = {n_z, n_z, n_r, n_r, n_theta, n_theta};
+    for (int i = 0; i < 6; ++i) {
+      std::vector<double> t = cyl::xform_tables(kinds[i], lens[i], P->xd[i]);
+      P->xoff[i] = (long long)xt.size();
+      xt.insert(xt.end(), t.begin(), t.end());
+      if (xt.size() & 1) xt.push_back(0.0);          // keep every block 16-byte aligned
+    }
+    e = upload(&P->d_xtab, xt.data(), xt.size());
+  }
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc((void **)&P->d_tmp[i], P->N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));

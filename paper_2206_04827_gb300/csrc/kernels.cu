@@ -651,13 +651,29 @@ __device__ __forceinline__ void vertical_tw2(double *__restrict__ row, const dou
 }
 
 // A group of threads that processes one item: the whole CTA (named barrier 0)
-// or one of G equal slices of it (named barriers 1 .. G).
+// or one of G equal slices of it (named barriers 1 .. G).  In cluster mode
+// the item is shared by the nparts CTAs of a thread-block cluster; this CTA
+// is part `part` and owns an equal range of the item's columns (radial
+// sweeps, right side, expansion) and rows (vertical sweeps).  csync() orders
+// the phases whose data cross CTAs: a cluster-wide barrier with release /
+// acquire semantics (the item's arrays live in global memory), else the
+// group's own barrier.
 struct Grp {
   int tid, nth, bar;
+  int part = 0, nparts = 1;
   __device__ __forceinline__ void sync() const {
     if (bar == 0) __syncthreads();
     else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nth) : "memory");
   }
+  __device__ __forceinline__ void csync() const {
+    if (nparts > 1)
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else
+      sync();
+  }
+  // [lo, hi) of this part's share of n
+  __device__ __forceinline__ int lo(int n) const { return (int)((long long)n * part / nparts); }
+  __device__ __forceinline__ int hi(int n) const { return (int)((long long)n * (part + 1) / nparts); }
 };
 
 // J iterations of Algorithm 1 on one item from X_0 = 0: right side in Fa,
@@ -697,6 +713,8 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
                                                double *S, const double *Fa, int ldF, long long &c, long long c0,
                                                long long c_end, bool &timed_out) {
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz, ld = a.ld, J = it.J;
+  // this part's columns (radial chains) and rows (vertical chains)
+  const int cb0 = gp.lo(W), cb1 = gp.hi(W), rb0 = gp.lo(nsl * M), rb1 = gp.hi(nsl * M);
   for (int jt = 0; jt < J; ++jt, ++c) {
     const int buf = (int)(c & 1);
     if (gp.tid == 0 && c + 1 < c_end && !a.test_no_tma) {
@@ -710,36 +728,38 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const bool bottom = gp.tid >= xh;
     const int chain = gp.tid - (bottom ? xh : 0);
     if (TW && !TRANS && it.twr) {
-      if (chain < W) {
-        if (jt == 0) radial_tw1<true, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
-        else radial_tw1<false, UNR>(S + chain, Fa + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+      const int col = cb0 + chain;
+      if (col < cb1) {
+        if (jt == 0) radial_tw1<true, UNR>(S + col, Fa + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+        else radial_tw1<false, UNR>(S + col, Fa + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
       }
       gp.sync();
-      if (chain < W) radial_tw2<UNR>(S + chain, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+      if (col < cb1) radial_tw2<UNR>(S + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
     } else {
-      for (int col = gp.tid; col < W; col += gp.nth) {
+      for (int col = cb0 + gp.tid; col < cb1; col += gp.nth) {
         if (jt == 0) radial_sweep<true, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
         else radial_sweep<false, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
       }
     }
-    gp.sync();
+    gp.csync();
     if (TW && !TRANS && it.twz) {
-      const int sl = chain / M, aa = chain - sl * M;
+      const int r = rb0 + chain;
+      const int sl = r / M, aa = r - sl * M;
       double *rowp = S + aa * ld + sl * Nz;
-      if (chain < nsl * M) vertical_tw1<UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+      if (r < rb1) vertical_tw1<UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
       gp.sync();
-      if (chain < nsl * M) {
+      if (r < rb1) {
         if (jt + 1 == J) vertical_tw2<true, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
         else vertical_tw2<false, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
       }
     } else {
-      for (int r = gp.tid; r < nsl * M; r += gp.nth) {
+      for (int r = rb0 + gp.tid; r < rb1; r += gp.nth) {
         const int sl = r / M, aa = r - sl * M;
         if (jt + 1 == J) vertical_sweep<true, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
         else vertical_sweep<false, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
       }
     }
-    gp.sync();
+    gp.csync();
   }
   (void)ldF;
 }
@@ -760,6 +780,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
                                                      bool &timed_out) {
   const int tid = gp.tid, nth = gp.nth;
   const int M = it.M, Nz = it.Nz, nsl = it.nsl, W = nsl * Nz;
+  const int cb0 = gp.lo(W), Wp = gp.hi(W) - cb0;    // this part's columns of the item
   const int ld = a.ld;
   const int m = it.m, n = it.n;
   const long long slice = (long long)m * n;
@@ -785,8 +806,8 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     // Right side of eq. HelmholtzMatEqn, E = trunc(R_2 (delta X + kappa g) C02^T), in two
     // banded passes: T1 = (delta X + kappa g) C02^T on the class rows, then E = R_2 T1
     // (delta X = X_n for BDF1, sum_i beta_i X_{n-i} from the history ring otherwise).
-    for (int e = tid; e < it.Mfull * W; e += nth) {
-      const int ap = e / W, cc = e - ap * W;
+    for (int e = tid; e < it.Mfull * Wp; e += nth) {
+      const int ap = e / Wp, cc = cb0 + (e - ap * Wp);
       const int sl = cc / Nz, b = cc - sl * Nz;
       const int i = it.pr + 2 * ap, j = it.pz + 2 * b;
       const size_t row = (size_t)(it.s0 + sl) * slice + (size_t)i * n;
@@ -812,8 +833,8 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     gp.sync();
     const double *corr = a.corr ? a.corr + it.xoff : nullptr;
-    for (int e = tid; e < M * W; e += nth) {
-      const int aa = e / W, cc = e - aa * W;
+    for (int e = tid; e < M * Wp; e += nth) {
+      const int aa = e / Wp, cc = cb0 + (e - aa * Wp);
       double acc = 0.0;
 #pragma unroll
       for (int s = -1; s <= 3; ++s) {
@@ -831,11 +852,11 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     adi_iterations<false, UNR, TW>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
-    const int Wf = nsl * it.Nzfull;
+    const int Wf = nsl * it.Nzfull, f0 = gp.lo(Wf), Wfp = gp.hi(Wf) - f0;
     const bool do_ck = a.ckpt && ((step + 1) % a.ckpt_every == 0);
     double *ck = do_ck ? a.ckpt + it.xoff + (size_t)((step + 1) / a.ckpt_every) * (size_t)a.p * slice : nullptr;
-    for (int e = tid; e < it.Mfull * Wf; e += nth) {
-      const int ap = e / Wf, cc = e - ap * Wf;
+    for (int e = tid; e < it.Mfull * Wfp; e += nth) {
+      const int ap = e / Wfp, cc = f0 + (e - ap * Wfp);
       const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
       const double *Ys = S + sl * Nz;
       const bool r0 = ap - 1 >= 0, r1 = ap < M, c0b = b - 1 >= 0, c1 = b < Nz;
@@ -851,8 +872,8 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     if (a.zero_other) {
       const int po = 1 - it.pr, Mo = (m - po + 1) / 2;
-      for (int e = tid; e < Mo * Wf; e += nth) {
-        const int ap = e / Wf, cc = e - ap * Wf;
+      for (int e = tid; e < Mo * Wfp; e += nth) {
+        const int ap = e / Wfp, cc = f0 + (e - ap * Wfp);
         const int sl = cc / it.Nzfull, b = cc - sl * it.Nzfull;
         const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(po + 2 * ap) * n + it.pz + 2 * b;
         const double x = lift ? lift[o] : 0.0;
@@ -860,7 +881,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
         if (ck) ck[o] = x;
       }
     }
-    gp.sync();
+    gp.csync();
     Xsrc = Xout;
     if (ring) base = (base + a.hist_b - 1) % a.hist_b;
   }
@@ -893,6 +914,68 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   long long c = 0;
   process_item_forward<S_SMEM ? 2 : 8, TW>(gp, a, it, sh, S, Fa, c, timed_out);
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+// Cluster mode, for items whose work arrays fit no SM's shared memory (grids
+// of about 220 points per axis and more): the a.cluster CTAs of a
+// thread-block cluster share one item, whose iterate S and right side Fa
+// stay in the item's global work area.  Each CTA owns at most 128 chains of
+// every sweep and runs them as twisted solves (two threads per chain, 256
+// threads, two warps per SM sub-partition); the phases that read other
+// CTAs' results meet at cluster barriers.  Only (resident CTAs / a.cluster)
+// items are live at a time, so their work arrays stay in L2 (at 512^3: 38
+// items x 2.1 MB) instead of streaming through DRAM every ADI iteration.
+template <int UNR>
+__global__ void __launch_bounds__(256, 1) adi_cluster_kernel(const AdiArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  const int item = blockIdx.x / a.cluster;
+  const Item it = a.items[item];
+  Grp gp{(int)threadIdx.x, (int)blockDim.x, 0};
+  gp.part = blockIdx.x - item * a.cluster;            // rank in the cluster (clusters tile the grid along x)
+  gp.nparts = a.cluster;
+  AdiShared sh;
+  sh.rlen = a.maxM * RSTRIDE + RTWIST;
+  sh.zlen = a.maxNz * ZSTRIDE + ZTWIST;
+  sh.RB0 = sm;
+  sh.ZB0 = sm + 2 * sh.rlen;
+  sh.bar = bar;
+  sh.xs = sh.ZB0 + 2 * sh.zlen;
+  sh.xhalf = a.twist_half;
+  double *gw = a.gwork + (size_t)item * a.gwork_per_item;
+  double *S = gw, *Fa = gw + (size_t)a.smem_rows * a.ld;
+  init_bars(gp, bar);
+  bool timed_out = false;
+  long long c = 0;
+  process_item_forward<UNR, true>(gp, a, it, sh, S, Fa, c, timed_out);
+  if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
+}
+
+size_t adi_cluster_smem_bytes(int maxM, int maxNz, int twist_half) {
+  const size_t d = 2 * ((size_t)maxM * RSTRIDE + RTWIST + (size_t)maxNz * ZSTRIDE + ZTWIST) +
+                   (size_t)TW_SLOTS * twist_half;
+  return d * sizeof(double);
+}
+
+cudaError_t launch_adi_cluster(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
+  if (a.cluster < 2 || a.cluster > 8 || threads > 256 || a.twist_half * 2 != threads) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(adi_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.nitems * a.cluster), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, adi_cluster_kernel<8>, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 // Persistent batch kernel: the CTA is split into G groups of blockDim.x / G
@@ -1205,19 +1288,16 @@ __global__ void lift_correction_kernel(const AdiArgs a, const double *__restrict
   }
 }
 
-cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
-                        double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
-                        int threads, cudaStream_t st) {
-  const long long N = (long long)a.p * a.m * a.n;
-  lift_values_kernel<<<(int)std::min<long long>((N + 255) / 256, 152LL * 16), 256, 0, st>>>(bc, Wv, a.p, a.m, a.n);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // values -> coefficients of W (the same three axis transforms as cyl_vals2coeffs)
-  if ((e = launch_axis_matvec(Wv, tmp0, Wz, (long long)a.p * a.m, a.n, 1, st)) != cudaSuccess) return e;
-  if ((e = launch_axis_matvec(tmp0, tmp1, Wr, a.p, a.m, a.n, st)) != cudaSuccess) return e;
-  if ((e = launch_axis_matvec(tmp1, Wc_out, Wt, 1, a.p, (long long)a.m * a.n, st)) != cudaSuccess) return e;
-  // corr is written (and later read) only at the items' class positions
-  lift_correction_kernel<<<a.nitems, threads, 0, st>>>(a, Wc_out, corr, c0, c1);
+cudaError_t launch_lift_values(const double *bc, double *Wv, int p, int m, int n, cudaStream_t st) {
+  const long long N = (long long)p * m * n;
+  lift_values_kernel<<<(int)std::min<long long>((N + 255) / 256, 152LL * 16), 256, 0, st>>>(bc, Wv, p, m, n);
+  return cudaGetLastError();
+}
+
+// corr is written (and later read) only at the items' class positions
+cudaError_t launch_lift_correction(const AdiArgs &a, const double *Wc, double *corr, double c0, double c1, int threads,
+                                   cudaStream_t st) {
+  lift_correction_kernel<<<a.nitems, threads, 0, st>>>(a, Wc, corr, c0, c1);
   return cudaGetLastError();
 }
 
@@ -1365,6 +1445,7 @@ static cudaError_t launch_adi_level(const AdiArgs &a, int threads, size_t smem, 
 // budget of 255 per thread; the twisted sweeps get instantiations of their own.
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
+  if (a.cluster > 1) return launch_adi_cluster(a, threads, smem, st);
   if (a.twist_half > 0 && threads > 256) return cudaErrorInvalidValue;
   if (a.use_smem == 2) return launch_adi_level<true, true>(a, threads, smem, st);
   if (a.use_smem == 1) return launch_adi_level<true, false>(a, threads, smem, st);

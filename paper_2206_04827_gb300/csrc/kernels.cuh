@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "plan.hpp"
 
 namespace cyl {
@@ -45,6 +47,7 @@ struct AdiArgs {
   const double *lift;      // coefficients of the lifting W of the boundary data, or NULL
   const double *corr;      // right-side correction of the lifted problem (class positions), or NULL
   int test_no_tma;         // failure-detection test: never start table copies, so waits run out
+  int cluster;             // > 1: CTAs of a thread-block cluster per item (work arrays in global memory)
 };
 
 constexpr int CYL_ERR_TIMEOUT = 4;
@@ -72,9 +75,9 @@ struct AdjointArgs {
 };
 
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st);
-cudaError_t launch_lift(const AdiArgs &a, const double *bc, double *Wv, double *Wc_out, double *corr, double c0,
-                        double c1, const double *Wt, const double *Wr, const double *Wz, double *tmp0, double *tmp1,
-                        int threads, cudaStream_t st);
+cudaError_t launch_lift_values(const double *bc, double *Wv, int p, int m, int n, cudaStream_t st);
+cudaError_t launch_lift_correction(const AdiArgs &a, const double *Wc, double *corr, double c0, double c1, int threads,
+                                   cudaStream_t st);
 cudaError_t launch_disk_poisson(const Item *items, int nitems, const double *fac, const double *F, double *U,
                                 int n, long long slice, int zero_other, int threads, cudaStream_t st);
 constexpr int kMaxSlots = 5;
@@ -93,6 +96,29 @@ cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int b
                          cudaStream_t st);
 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st);
+// cluster mode (a.cluster CTAs per item, 2 x twist_half threads, twisted tables)
+size_t adi_cluster_smem_bytes(int maxM, int maxNz, int twist_half);
+cudaError_t launch_adi_cluster(const AdiArgs &a, int threads, size_t smem, cudaStream_t st);
+
+// Chirp-z (Bluestein) line transforms of Section 2 (xform.cu): kind 0 DCT-I
+// forward, 1 DCT-I inverse (line length L = the number of Chebyshev
+// points), 2 DFT forward to half-complex, 3 DFT inverse from half-complex
+// (L = p).  The table block (doubles) holds pre [2A] and post [2B]
+// multipliers, the bit-reversed kernel spectrum scaled by 1/P [2P] and the
+// FFT twiddles exp(-2 pi i k / P), k < P/2 [P].
+struct XformDesc {
+  int kind = 0, L = 0, P = 0, logP = 0, A = 0, B = 0, ia0 = 0, jb0 = 0;
+  long long pre_off = 0, post_off = 0, H_off = 0, tw_off = 0;
+};
+constexpr int kMaxXformFfts = 16;     // complex FFTs per CTA
+constexpr int kMaxXformP = 8192;      // largest FFT length (shared memory: 16 P bytes per FFT)
+std::vector<double> xform_tables(int kind, int L, XformDesc &d);
+int xform_ffts_per_cta(int P);
+size_t xform_smem_bytes(int P);
+// Lines along one axis: outer x inner lines of L elements, element a of line
+// (o, i) at o * L * inner + a * inner + i (in may equal out).
+cudaError_t launch_xform(const double *in, double *out, const double *tab, const XformDesc &d, long long outer,
+                         long long inner, int sms, cudaStream_t st);
 
 // out[o][j][i] = sum_t W[j][t] in[o][t][i]  (dense transform along one axis)
 cudaError_t launch_axis_matvec(const double *in, double *out, const double *W, long long outer, int L,

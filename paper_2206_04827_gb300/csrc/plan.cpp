@@ -303,59 +303,6 @@ bool zolotarev(double a, double b, double c, double d, double tol, Shifts &S) {
   return true;
 }
 
-// -------------------------------------------------------- transform matrices
-// Section 2, interpolant f*: DCT-I in r and z, DFT in theta, on the grid of
-// Definition "grid": r_a = cos((m-1-a) pi / (m-1)), theta_l = (2l - p) pi / p.
-
-double cos_pi_frac(long long num, long long den) {   // cos(num * pi / den), argument reduced exactly
-  long long r = num % (2 * den);
-  if (r < 0) r += 2 * den;
-  return std::cos(PI * (double)r / (double)den);
-}
-
-double sin_pi_frac(long long num, long long den) {
-  long long r = num % (2 * den);
-  if (r < 0) r += 2 * den;
-  return std::sin(PI * (double)r / (double)den);
-}
-
-void cheb_matrices(int m, std::vector<double> &Wf, std::vector<double> &Wi) {
-  Wf.assign((size_t)m * m, 0.0);
-  Wi.assign((size_t)m * m, 0.0);
-  for (int j = 0; j < m; ++j)
-    for (int a = 0; a < m; ++a) {
-      const double T = cos_pi_frac((long long)j * (m - 1 - a), m - 1);   // T_j(r_a)
-      const double wj = (j == 0 || j == m - 1) ? 0.5 : 1.0;
-      const double wa = (a == 0 || a == m - 1) ? 0.5 : 1.0;
-      Wf[(size_t)j * m + a] = 2.0 / (m - 1) * wj * wa * T;               // c_j = sum_a Wf[j][a] f_a
-      Wi[(size_t)a * m + j] = T;                                          // f_a = sum_j Wi[a][j] c_j
-    }
-}
-
-void theta_matrices(int p, std::vector<double> &Wf, std::vector<double> &Wi) {
-  Wf.assign((size_t)p * p, 0.0);
-  Wi.assign((size_t)p * p, 0.0);
-  const int h = p / 2;
-  for (int l = 0; l < p; ++l) {
-    // w theta_l = w (2l - p) pi / p
-    Wf[(size_t)0 * p + l] = 1.0 / p;
-    Wi[(size_t)l * p + 0] = 1.0;
-    for (int w = 1; w < h; ++w) {
-      const double cw = cos_pi_frac((long long)w * (2 * l - p), p);
-      const double sw = sin_pi_frac((long long)w * (2 * l - p), p);
-      Wf[(size_t)(2 * w - 1) * p + l] = cw / p;       // Re c_w
-      Wf[(size_t)(2 * w) * p + l] = -sw / p;          // Im c_w
-      Wi[(size_t)l * p + (2 * w - 1)] = 2.0 * cw;
-      Wi[(size_t)l * p + (2 * w)] = -2.0 * sw;
-    }
-    if (p >= 2) {
-      const double cn = cos_pi_frac((long long)h * (2 * l - p), p);   // Nyquist basis value
-      Wf[(size_t)(p - 1) * p + l] = cn / p;
-      Wi[(size_t)l * p + (p - 1)] = cn;
-    }
-  }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------- elliptic functions
@@ -570,7 +517,9 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
   // twisted solves only where both sweeps' chains (two slices x class size) fit kTwistMaxChains:
   // there the second half of the threads doubles the warps per SM sub-partition
   const int maxclass = std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1]));
-  const bool tw_ok = (twist == 1 && 2 * maxclass <= kTwistMaxChains) || (twist == 2 && maxclass <= kTwistMaxChains);
+  // twist == 3 (cluster plans): every item, each CTA of its cluster owning at most kTwistMaxChains chains
+  const bool tw_ok = (twist == 1 && 2 * maxclass <= kTwistMaxChains) || (twist == 2 && maxclass <= kTwistMaxChains) ||
+                     twist == 3;
   for (int kind = 0; kind < kNumKinds; ++kind) {
     KindTables &KT = hp.kind[kind];
     KT = KindTables();
@@ -739,9 +688,6 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
     });
     KT.built = true;
   }
-  cheb_matrices(m, hp.Wr_f, hp.Wr_i);
-  cheb_matrices(n, hp.Wz_f, hp.Wz_i);
-  theta_matrices(p, hp.Wt_f, hp.Wt_i);
   return std::string();
 }
 

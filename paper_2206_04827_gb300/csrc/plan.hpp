@@ -126,8 +126,6 @@ struct HostPlan {
   long long r2off[2] = {0, 0};          // R_2 band tables per radial class
   KindTables kind[kNumKinds];           // 0 = Poisson, 1..bdf_order = BDF 1..b
   std::vector<double> factors;          // all radial and vertical factor rows + rhs bands
-  // transform matrices (row-major, out index major): forward and inverse
-  std::vector<double> Wr_f, Wr_i, Wz_f, Wz_i, Wt_f, Wt_i;
 
   // radial block operators per k (lazily usable by introspection)
   Band Cblk(int pr) const;
@@ -139,7 +137,9 @@ struct HostPlan {
 // Build everything on the host.  Returns an empty string on success, else a message.
 // twist: 0 = one-sided sweeps only; 1 = twisted (two-sided) solves where both
 // sweeps of a two-slice item have at most kTwistMaxChains chains; 2 = where
-// one slice has (batch plans, which split twisted pairs into single slices).
+// one slice has (batch plans, which split twisted pairs into single slices);
+// 3 = every item (cluster plans: each CTA of an item's cluster owns at most
+// kTwistMaxChains chains of every sweep).
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
                             unsigned flags, int bdf_order = 1, int twist = 1);
 

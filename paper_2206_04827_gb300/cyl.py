@@ -23,7 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # status codes and flags (include/cyl.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 WITH_POISSON, WITH_HEAT, BOTH_PARITIES, HOST_ONLY, FORCE_GLOBAL, TEST_NO_TMA, WITH_BC = 1, 2, 4, 8, 16, 32, 64
-PLAIN_SWEEPS, WITH_DISK = 128, 256
+PLAIN_SWEEPS, WITH_DISK, FORCE_CLUSTER = 128, 256, 512
 VALUES, COEFFS = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -73,6 +73,7 @@ _sig = {
     'cyl_batch_autotune': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
     'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+    'cyl_xform_table': (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _c_double_p]),
     'cyl_fp64_fma_probe': (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _c_double_p, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -357,6 +358,16 @@ def plan_flops(handle, which, nsteps, transposed):
     _check(_lib.cyl_plan_flops(handle, int(which), int(nsteps), int(bool(transposed)), ctypes.byref(f)),
            'cyl_plan_flops')
     return f.value
+
+
+def xform_table(kind, L):
+    """(info dict, table) of one chirp-z line transform (include/cyl.h: cyl_xform_table)."""
+    info = (ctypes.c_int * 11)()
+    _check(_lib.cyl_xform_table(int(kind), int(L), info, None), 'cyl_xform_table')
+    tab = (ctypes.c_double * info[10])()
+    _check(_lib.cyl_xform_table(int(kind), int(L), info, tab), 'cyl_xform_table')
+    keys = ('P', 'logP', 'A', 'B', 'ia0', 'jb0', 'pre_off', 'post_off', 'H_off', 'tw_off', 'size')
+    return dict(zip(keys, list(info))), np.array(tab)
 
 
 def fp64_fma_probe(sink, blocks, threads, iters, stream):

@@ -265,26 +265,52 @@ def test_item_tables_drive_adi_to_the_direct_solve(cyl, which):
         nitems += 1
     assert nitems > 0
     for item in range(0, nitems, 3):
-        info, _, _ = plan.item_tables(which, item, 0)
-        M, Nz, J, kr, kz = info['M'], info['Nz'], info['J'], info['twr'], info['twz']
+        kr, kz = _drive_item_to_direct_solve(cyl, plan, which, item, rng)
         seen_twisted |= bool(kr and kz)
-        A, C = plan.operator(0, which, info['k'], info['pr']), plan.operator(1, which, info['k'], info['pr'])
-        B, D = plan.operator(2, which, info['k'], info['pz']), plan.operator(3, which, info['k'], info['pz'])
-        ii, jj = np.meshgrid(np.arange(M), np.arange(Nz), indexing='ij')
-        E = rng.standard_normal((M, Nz)) * 1.3 ** (-(ii + jj))
-        U = np.zeros((M, Nz))
-        X = None
-        for j in range(J):
-            _, rad, ver = plan.item_tables(which, item, j)
-            rrec, Rr = rad[:M * 12].reshape(M, 12), rad[M * 12:]
-            vrec, Rz = ver[:Nz * 8].reshape(Nz, 8), ver[Nz * 8:]
-            Z = np.stack([_radial_column(rrec, Rr, U[:, c], E[:, c], j == 0, kr) for c in range(Nz)], axis=1)
-            rows = [_vertical_row(vrec, Rz, Z[a], kz) for a in range(M)]
-            X = np.stack([r[0] for r in rows])
-            U = np.stack([r[1] for r in rows])
-        Xd = sy.solve_kron(A, B, C, D, E)
-        assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max(), (item, kr, kz)
     assert seen_twisted
+    plan.close()
+
+
+def _drive_item_to_direct_solve(cyl, plan, which, item, rng):
+    """Algorithm 1 on one item from its factor records against the dense
+    Kronecker solve of its block equation; returns the twisted splits."""
+    info, _, _ = plan.item_tables(which, item, 0)
+    M, Nz, J, kr, kz = info['M'], info['Nz'], info['J'], info['twr'], info['twz']
+    A, C = plan.operator(0, which, info['k'], info['pr']), plan.operator(1, which, info['k'], info['pr'])
+    B, D = plan.operator(2, which, info['k'], info['pz']), plan.operator(3, which, info['k'], info['pz'])
+    ii, jj = np.meshgrid(np.arange(M), np.arange(Nz), indexing='ij')
+    E = rng.standard_normal((M, Nz)) * 1.3 ** (-(ii + jj))
+    U = np.zeros((M, Nz))
+    X = None
+    for j in range(J):
+        _, rad, ver = plan.item_tables(which, item, j)
+        rrec, Rr = rad[:M * 12].reshape(M, 12), rad[M * 12:]
+        vrec, Rz = ver[:Nz * 8].reshape(Nz, 8), ver[Nz * 8:]
+        Z = np.stack([_radial_column(rrec, Rr, U[:, c], E[:, c], j == 0, kr) for c in range(Nz)], axis=1)
+        rows = [_vertical_row(vrec, Rz, Z[a], kz) for a in range(M)]
+        X = np.stack([r[0] for r in rows])
+        U = np.stack([r[1] for r in rows])
+    Xd = sy.solve_kron(A, B, C, D, E)
+    assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max(), (item, kr, kz)
+    return kr, kz
+
+
+def test_cluster_plans_twist_every_item(cyl):
+    """Cluster plans (several CTAs per item, at most 128 chains each) carry
+    twisted two-sided solves on items whose chains exceed what one CTA
+    twists, and Algorithm 1 from those records still reaches the direct
+    solve; without cluster mode such items keep one-sided LU records."""
+    m, n, p = 140, 132, 8
+    plain = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=True, heat=True, host_only=True)
+    info, _, _ = plain.item_tables(1, 0, 0)
+    assert info['twr'] == 0 and info['twz'] == 0
+    plain.close()
+    plan = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=True, heat=True, host_only=True,
+                    extra_flags=cyl.FORCE_CLUSTER)
+    rng = np.random.default_rng(17)
+    for which, item in ((0, 0), (1, 3)):
+        kr, kz = _drive_item_to_direct_solve(cyl, plan, which, item, rng)
+        assert kr > 0 and kz > 0
     plan.close()
 
 
