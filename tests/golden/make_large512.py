@@ -4,13 +4,16 @@ dt 1e-4 and forcing f starting from u) on sampled theta-slices and sampled
 coefficients.  Inputs: paper_2206_04827_gb300.inputs.smooth_coeffs(512, 512,
 512, decay 1.1) from seed 1002 (the 512^3 workload's generator).  Calls only
 oracle/ (QZ Bartels-Stewart with one step of iterative refinement per solve;
-the plain direct solve drifts to ~1e-11 at this size).  Slices are
-independent, so only the sampled slices are solved.  About 25 minutes on an
+the plain direct solve drifts to ~1e-11 at this size; the refinement's
+residuals are formed in np.longdouble, whose mantissa width and the machine
+are stored with the values).  Slices are independent, so only the sampled
+slices are solved.  About 25 minutes on an
 8-core host; run from the repository root:
 
     python tests/golden/make_large512.py
 """
 import os
+import platform
 import sys
 
 import numpy as np
@@ -36,7 +39,8 @@ def main():
     ix = np.ix_(SLICES, IDX, IDX)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), 'large512_sampled.npz')
     np.savez_compressed(out, slices=np.array(SLICES), idx=np.array(IDX), poisson=u[ix], heat=T[ix],
-                        alpha=ALPHA, dt=DT, hsteps=HSTEPS, seed=SEED)
+                        alpha=ALPHA, dt=DT, hsteps=HSTEPS, seed=SEED,
+                        longdouble_mantissa_bits=np.finfo(np.longdouble).nmant, machine=platform.machine())
     print('wrote', out)
 
 
