@@ -462,13 +462,16 @@ cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int pari
  * tables the kernels read; layout in the library's plan header: radial
  * records of 12 doubles per class row, vertical records of 8 per class
  * column, plus the interface maps of twisted solves).  transposed = 1 gives
- * the records of the transposed system the adjoint kernels solve (heat kinds
- * only, else CYL_ESTATE; always one-sided).  info[8] receives {M, Nz, J, twr,
- * twz, k, parity_r, parity_z}; twr / twz are the split rows of the twisted
- * radial / vertical solves (0: plain LU sweep).  radial needs M*12 + (twr and
- * not transposed ? 24 : 0) doubles, vertical Nz*8 + (twz and not transposed ?
- * 16 : 0); either may be NULL.  Items are numbered as the plan lists them
- * (which as above). */
+ * the records of the transposed system A^T X B + C^T X D = E the adjoint
+ * kernels solve (heat kinds only, else CYL_ESTATE): the records, in the
+ * forward layout, of the flipped transposes J A^T J, J C^T J, J B^T J,
+ * J D^T J (J reverses the index order), which solve the transposed system
+ * on index-reversed arrays; twisted where the forward records are, except in
+ * cluster plans.  info[8] receives {M, Nz, J, twr, twz, k, parity_r,
+ * parity_z}; twr / twz are the split rows of the requested records' twisted
+ * radial / vertical solves (0: plain LU sweep).  radial needs M*12 + (twr ?
+ * 24 : 0) doubles, vertical Nz*8 + (twz ? 16 : 0); either may be NULL.  Items
+ * are numbered as the plan lists them (which as above). */
 cyl_status cyl_plan_item_tables(cyl_plan_t plan, int which, int item, int j, int transposed, int *info,
                                 double *radial, double *vertical);
 

@@ -960,12 +960,12 @@ cyl_status cyl_plan_item_tables(cyl_plan_t P, int which, int item, int j, int tr
   if (item >= (int)KT.items.size()) return CYL_EINVAL;
   const Item &it = KT.items[item];
   if (j >= it.J) return CYL_EINVAL;
-  info[0] = it.M; info[1] = it.Nz; info[2] = it.J; info[3] = it.twr; info[4] = it.twz;
+  const int twr = transposed ? it.twrT : it.twr, twz = transposed ? it.twzT : it.twz;
+  info[0] = it.M; info[1] = it.Nz; info[2] = it.J; info[3] = twr; info[4] = twz;
   info[5] = it.k; info[6] = it.pr; info[7] = it.pz;
   if (transposed && (it.roffT < 0 || it.zoffT < 0)) return CYL_ESTATE;
-  // the transposed (adjoint) tables are one-sided: no interface maps
-  const size_t rs = (size_t)it.M * cyl::RSTRIDE + (!transposed && it.twr ? cyl::RTWIST : 0);
-  const size_t zs = (size_t)it.Nz * cyl::ZSTRIDE + (!transposed && it.twz ? cyl::ZTWIST : 0);
+  const size_t rs = (size_t)it.M * cyl::RSTRIDE + (twr ? cyl::RTWIST : 0);
+  const size_t zs = (size_t)it.Nz * cyl::ZSTRIDE + (twz ? cyl::ZTWIST : 0);
   const double *F = P->hp.factors.data();
   const long long ro = transposed ? it.roffT : it.roff, zo = transposed ? it.zoffT : it.zoff;
   if (radial) std::memcpy(radial, F + ro + (size_t)j * rs, rs * sizeof(double));

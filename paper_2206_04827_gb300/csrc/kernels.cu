@@ -11,7 +11,8 @@
 // adi_batch_kernel  the same per item, for many problems: persistent CTAs of G
 //                   thread groups pull items (largest first) from a queue.
 // adi_adjoint_kernel  the transposed step map run backward over the steps
-//                   (BDF1, or the multistep ring of BDF b).
+//                   (BDF1, or the multistep ring of BDF b), through the
+//                   forward sweeps on index-reversed arrays.
 // axis_matvec       dense value <-> coefficient transform along one axis
 //                   (Section 2: DCT-I in r and z, DFT in theta).
 // disk_poisson      the horizontal (disk) Poisson solve of Section 4.
@@ -88,8 +89,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 //   vertical: X_{j+1} = Z (D + qB)^-T,  U' = X_{j+1} (D + p'B)^T
 // which is the paper's two half-steps (with the signs corrected so that the
 // fixed point solves A X B^T + C X D^T = E) after eliminating the C solve.
-// TRANS selects the transposed system A^T X B + C^T X D = E (adjoint), whose
-// factor records have the same size with the band orientations swapped.
+// The adjoint's transposed system runs through the same sweeps (its records
+// are those of the flipped transposes, on index-reversed arrays).
 //
 // Every sweep loads the operands of the next row (column) one step ahead
 // into registers: with one warp per SM sub-partition an exposed shared-memory
@@ -99,13 +100,13 @@ __device__ __forceinline__ double comp(const double2 *a) {
   return (K & 1) ? a[K >> 1].y : a[K >> 1].x;
 }
 
-template <bool FIRST, bool TRANS, int UNR>
+template <bool FIRST, int UNR>
 __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const double *__restrict__ Fc, int ld,
                                              const double *__restrict__ RB, int M) {
-  constexpr int LO = TRANS ? 3 : 2, HI = TRANS ? 2 : 3;     // apply band offsets [-LO, HI]
-  constexpr int LBW = TRANS ? 3 : 2, UBW = TRANS ? 2 : 3;   // L and U bandwidths
-  constexpr int NF = (6 + LBW + 1) / 2;                     // double2 words read going down
-  constexpr int B0 = (6 + LBW) / 2;                         // first double2 word read going up
+  constexpr int LO = 2, HI = 3;                             // apply band offsets [-LO, HI]
+  constexpr int LBW = 2, UBW = 3;                           // L and U bandwidths
+  constexpr int NF = 4;                                     // double2 words read going down ([0..7])
+  constexpr int B0 = 4;                                     // first double2 word read going up ([8..11])
   constexpr int NB = RSTRIDE / 2 - B0;
   const double2 *rb2 = reinterpret_cast<const double2 *>(RB);
   double w[LO + HI + 1];
@@ -150,12 +151,10 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
       for (int k = 0; k < LO + HI; ++k) w[k] = w[k + 1];
     }
     // L terms, oldest first: only the last one waits for the previous row
-    if (LBW == 3) acc = fma(comp<(LBW == 3 ? 8 : 7)>(rec), y[LBW - 1], acc);
     acc = fma(comp<7>(rec), y[1], acc);
     acc = fma(comp<6>(rec), y[0], acc);
     col[i * ld] = acc;
-#pragma unroll
-    for (int l = LBW - 1; l > 0; --l) y[l] = y[l - 1];
+    y[1] = y[0];
     y[0] = acc;
   }
   double z[UBW];
@@ -176,26 +175,23 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
 #pragma unroll
       for (int k = 0; k < NB; ++k) nb[k] = rb2[(i - 1) * (RSTRIDE / 2) + B0 + k];
     }
-    // U terms carry the pivot; the newest value z_{i+1} enters last
-    double acc = comp<11 - 2 * B0>(cb) * yv;
-    if (UBW == 3) acc = fma(comp<(UBW == 3 ? 8 + LBW - 2 * B0 : 7 + LBW - 2 * B0)>(cb), z[UBW - 1], acc);
-    acc = fma(comp<7 + LBW - 2 * B0>(cb), z[1], acc);
-    const double zi = fma(comp<6 + LBW - 2 * B0>(cb), z[0], acc);
+    // U terms carry the pivot; the newest value z_{i+1} enters last  ([8..10] -U/U_ii, [11] (q-p)/U_ii)
+    double acc = comp<3>(cb) * yv;
+    acc = fma(comp<2>(cb), z[2], acc);
+    acc = fma(comp<1>(cb), z[1], acc);
+    const double zi = fma(comp<0>(cb), z[0], acc);
     col[i * ld] = zi;
-#pragma unroll
-    for (int u = UBW - 1; u > 0; --u) z[u] = z[u - 1];
+    z[2] = z[1];
+    z[1] = z[0];
     z[0] = zi;
   }
 }
 
-template <bool LAST, bool TRANS, int UNR>
+template <bool LAST, int UNR>
 __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz) {
-  constexpr int LB = TRANS ? 2 : 1;                         // L bandwidth (U: 3 - LB)
-  constexpr int ALO = TRANS ? 2 : 1;                        // apply offsets [-ALO, 3 - ALO]
+  constexpr int ALO = 1;                                    // apply offsets [-1, 2]
   const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
-  double wq[LB];
-#pragma unroll
-  for (int l = 0; l < LB; ++l) wq[l] = 0.0;
+  double wq = 0.0;
   double rn = row[0];
   double2 cn = z2p[0];
 #pragma unroll UNR
@@ -206,21 +202,15 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
       rn = row[b + 1];
       cn = z2p[(b + 1) * 4];
     }
-    double w = r;
-    if (LB == 2) w = fma(c.y, wq[LB - 1], w);
-    w = fma(c.x, wq[0], w);
+    const double w = fma(c.x, wq, r);                       // [0] -L[c][c-1]
     row[b] = w;
-#pragma unroll
-    for (int l = LB - 1; l > 0; --l) wq[l] = wq[l - 1];
-    wq[0] = w;
+    wq = w;
   }
   double x1 = 0.0, x2 = 0.0, x3 = 0.0;                      // x_{b+1}, x_{b+2}, x_{b+3}
   double2 p01 = z2p[(Nz - 1) * 4], p23 = z2p[(Nz - 1) * 4 + 1], p45, p67;
   if (!LAST) { p45 = z2p[(Nz - 1) * 4 + 2]; p67 = z2p[(Nz - 1) * 4 + 3]; }
   double wn = row[Nz - 1];
-  double2 q45[ALO], q67[ALO];                               // apply records of columns b+1 .. b+ALO
-#pragma unroll
-  for (int t = 0; t < ALO; ++t) { q45[t] = make_double2(0.0, 0.0); q67[t] = make_double2(0.0, 0.0); }
+  double2 q45 = make_double2(0.0, 0.0), q67 = make_double2(0.0, 0.0);   // apply record of column b+1
 #pragma unroll UNR
   for (int b = Nz - 1; b >= 0; --b) {
     const double wb = wn;
@@ -233,47 +223,29 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
       p23 = z2p[(b - 1) * 4 + 1];
       if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
     }
-    // U terms carry the pivot; the newest value x_{b+1} enters last
-    double xb;
-    if (TRANS) {            // [0..1] -L, [2] -U/U_cc, [3] 1/U_cc
-      xb = fma(c23.x, x1, c23.y * wb);
-    } else {                // [0] -L, [1..2] -U/U_cc, [3] 1/U_cc
-      double v = fma(c23.x, x2, c23.y * wb);
-      xb = fma(c01.y, x1, v);
-    }
+    // U terms carry the pivot; the newest value x_{b+1} enters last ([1..2] -U/U_cc, [3] 1/U_cc)
+    const double v = fma(c23.x, x2, c23.y * wb);
+    const double xb = fma(c01.y, x1, v);
     if (LAST) {
       row[b] = xb;
     } else {
       if (b + ALO < Nz) {
-        const double2 a45 = q45[ALO - 1], a67 = q67[ALO - 1];
-        double u = a67.y * x3;
-        u = fma(a67.x, x2, u);
-        u = fma(a45.y, x1, u);
-        u = fma(a45.x, xb, u);
+        double u = q67.y * x3;
+        u = fma(q67.x, x2, u);
+        u = fma(q45.y, x1, u);
+        u = fma(q45.x, xb, u);
         row[b + ALO] = u;
       }
-#pragma unroll
-      for (int t = ALO - 1; t > 0; --t) { q45[t] = q45[t - 1]; q67[t] = q67[t - 1]; }
-      q45[0] = c45;
-      q67[0] = c67;
+      q45 = c45;
+      q67 = c67;
     }
     x3 = x2; x2 = x1; x1 = xb;
   }
-  if (!LAST) {              // columns 0 .. ALO-1 (x_{-1}, x_{-2} = 0); q[t] holds column t
-    if (ALO == 1) {
-      double u = q45[0].y * x1;
-      u = fma(q67[0].x, x2, u);
-      u = fma(q67[0].y, x3, u);
-      row[0] = u;
-    } else {
-      double u1 = q45[ALO - 1].y * x1;
-      u1 = fma(q67[ALO - 1].x, x2, u1);
-      u1 = fma(q67[ALO - 1].y, x3, u1);
-      if (Nz > 1) row[1] = u1;
-      double u0 = q67[0].x * x1;
-      u0 = fma(q67[0].y, x2, u0);
-      row[0] = u0;
-    }
+  if (!LAST) {              // column 0 (x_{-1} = 0); q holds column 0's apply record
+    double u = q45.y * x1;
+    u = fma(q67.x, x2, u);
+    u = fma(q67.y, x3, u);
+    row[0] = u;
   }
 }
 
@@ -688,15 +660,16 @@ struct AdiShared {
   int xhalf;      // threads per side of a twisted sweep (half the group)
 };
 
-template <bool TRANS>
+// TT: the transposed (adjoint) system's records instead of the forward ones.
+template <bool TT>
 __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs &a, const Item &it, long long c,
                                              long long c0) {
   const int jt = (int)((c - c0) % it.J), buf = (int)(c & 1);
-  const int rsz = it.M * RSTRIDE + ((!TRANS && it.twr) ? RTWIST : 0);
-  const int zsz = it.Nz * ZSTRIDE + ((!TRANS && it.twz) ? ZTWIST : 0);
+  const int rsz = it.M * RSTRIDE + ((TT ? it.twrT : it.twr) ? RTWIST : 0);
+  const int zsz = it.Nz * ZSTRIDE + ((TT ? it.twzT : it.twz) ? ZTWIST : 0);
   const unsigned rbytes = (unsigned)(rsz * sizeof(double));
   const unsigned zbytes = (unsigned)(zsz * sizeof(double));
-  const long long roff = TRANS ? it.roffT : it.roff, zoff = TRANS ? it.zoffT : it.zoff;
+  const long long roff = TT ? it.roffT : it.roff, zoff = TT ? it.zoffT : it.zoff;
   mbar_expect(&sh.bar[buf], rbytes + zbytes);
   bulk_g2s(sh.RB0 + buf * sh.rlen, a.fac + roff + (size_t)jt * rsz, rbytes, &sh.bar[buf]);
   bulk_g2s(sh.ZB0 + buf * sh.zlen, a.fac + zoff + (size_t)jt * zsz, zbytes, &sh.bar[buf]);
@@ -708,7 +681,7 @@ __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs 
 // TW: compiled with the twisted sweeps (items whose tables carry twisted
 // solves, twr / twz > 0); without it only the one-sided sweeps are compiled,
 // which keeps the register allocation of the plain kernels unchanged.
-template <bool TRANS, int UNR, bool TW = false>
+template <bool TT, int UNR, bool TW = false>
 __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &sh, const AdiArgs &a, const Item &it,
                                                double *S, const double *Fa, int ldF, long long &c, long long c0,
                                                long long c_end, bool &timed_out) {
@@ -719,7 +692,7 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const int buf = (int)(c & 1);
     if (gp.tid == 0 && c + 1 < c_end && !a.test_no_tma) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tables<TRANS>(sh, a, it, c + 1, c0);
+      issue_tables<TT>(sh, a, it, c + 1, c0);
     }
     if (!mbar_wait(&sh.bar[buf], (unsigned)((c >> 1) & 1), a.wait_limit)) timed_out = true;
     const double *RB = sh.RB0 + buf * sh.rlen;
@@ -727,36 +700,37 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const int xh = sh.xhalf;
     const bool bottom = gp.tid >= xh;
     const int chain = gp.tid - (bottom ? xh : 0);
-    if (TW && !TRANS && it.twr) {
+    const int twr = TT ? it.twrT : it.twr, twz = TT ? it.twzT : it.twz;
+    if (TW && twr) {
       const int col = cb0 + chain;
       if (col < cb1) {
-        if (jt == 0) radial_tw1<true, UNR>(S + col, Fa + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
-        else radial_tw1<false, UNR>(S + col, Fa + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+        if (jt == 0) radial_tw1<true, UNR>(S + col, Fa + col, ld, RB, M, twr, bottom, sh.xs + chain, xh);
+        else radial_tw1<false, UNR>(S + col, Fa + col, ld, RB, M, twr, bottom, sh.xs + chain, xh);
       }
       gp.sync();
-      if (col < cb1) radial_tw2<UNR>(S + col, ld, RB, M, it.twr, bottom, sh.xs + chain, xh);
+      if (col < cb1) radial_tw2<UNR>(S + col, ld, RB, M, twr, bottom, sh.xs + chain, xh);
     } else {
       for (int col = cb0 + gp.tid; col < cb1; col += gp.nth) {
-        if (jt == 0) radial_sweep<true, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
-        else radial_sweep<false, TRANS, UNR>(S + col, Fa + col, ld, RB, M);
+        if (jt == 0) radial_sweep<true, UNR>(S + col, Fa + col, ld, RB, M);
+        else radial_sweep<false, UNR>(S + col, Fa + col, ld, RB, M);
       }
     }
     gp.csync();
-    if (TW && !TRANS && it.twz) {
+    if (TW && twz) {
       const int r = rb0 + chain;
       const int sl = r / M, aa = r - sl * M;
       double *rowp = S + aa * ld + sl * Nz;
-      if (r < rb1) vertical_tw1<UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+      if (r < rb1) vertical_tw1<UNR>(rowp, ZB, Nz, twz, bottom, sh.xs + chain, xh);
       gp.sync();
       if (r < rb1) {
-        if (jt + 1 == J) vertical_tw2<true, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
-        else vertical_tw2<false, UNR>(rowp, ZB, Nz, it.twz, bottom, sh.xs + chain, xh);
+        if (jt + 1 == J) vertical_tw2<true, UNR>(rowp, ZB, Nz, twz, bottom, sh.xs + chain, xh);
+        else vertical_tw2<false, UNR>(rowp, ZB, Nz, twz, bottom, sh.xs + chain, xh);
       }
     } else {
       for (int r = rb0 + gp.tid; r < rb1; r += gp.nth) {
         const int sl = r / M, aa = r - sl * M;
-        if (jt + 1 == J) vertical_sweep<true, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
-        else vertical_sweep<false, TRANS, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+        if (jt + 1 == J) vertical_sweep<true, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
+        else vertical_sweep<false, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
       }
     }
     gp.csync();
@@ -1068,12 +1042,17 @@ cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int b
 
 // Adjoint of the BDF1 steps n = n_hi-1 .. n_lo for one item (the transpose of
 // adi_kernel's map, step by step in reverse):
-//   mu = S_r^T lam S_z;  Lambda = (A^T . B + C^T . D)^-1 mu by the transposed ADI;
+//   mu = S_r^T lam S_z;  Lambda = (A^T . B + C^T . D)^-1 mu by ADI;
 //   lam <- R_2^T Lambda C02 (class rows < m, class columns < n);
 //   dL/dg_n = kappa lam;  dL/dalpha += <lam, X_{n+1} - X_n - kappa g_n> / alpha
 // (the last identity follows from A Y B^T + C Y D^T = E, A = C - kappa alpha L,
 // D = -kappa alpha D2:  d/dalpha of the solve is (E - C Y B^T) / alpha).
-template <bool SMEM, int MAXT>
+// The transposed Sylvester solve is the forward-form system of the flipped
+// transposes J A^T J, ... on index-reversed arrays (J reverses the class
+// rows and, per slice, the class columns), so mu is written and Lambda read
+// in reversed order and the forward sweeps (twisted where the records are)
+// do the iterations with the transposed records.  Work arrays as adi_kernel.
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
 __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, AdjointArgs g) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -1085,15 +1064,19 @@ __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, A
   const int m = it.m, n = it.n;
   const long long slice = (long long)m * n, Ntot = (long long)a.p * slice;
   AdiShared sh;
-  sh.rlen = a.maxM * RSTRIDE;
-  sh.zlen = a.maxNz * ZSTRIDE;
+  sh.rlen = a.maxM * RSTRIDE + RTWIST;
+  sh.zlen = a.maxNz * ZSTRIDE + ZTWIST;
   sh.RB0 = sm;
   sh.ZB0 = sm + 2 * sh.rlen;
   sh.bar = bar;
-  sh.xs = nullptr;        // the transposed tables are never twisted
-  sh.xhalf = nth;
-  double *S = SMEM ? sh.ZB0 + 2 * sh.zlen : a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
-  double *Fa = S + (size_t)a.smem_rows * ld;
+  double *smem_next = sh.ZB0 + 2 * sh.zlen;
+  double *gw = a.gwork + (size_t)blockIdx.x * a.gwork_per_item;
+  double *S = S_SMEM ? smem_next : gw;
+  if (S_SMEM) smem_next += (size_t)a.smem_rows * ld;
+  double *Fa = F_SMEM ? smem_next : gw + (S_SMEM ? 0 : (size_t)a.smem_rows * ld);
+  if (F_SMEM) smem_next += (size_t)a.maxM * ld;
+  sh.xs = a.twist_half ? smem_next : nullptr;
+  sh.xhalf = a.twist_half ? a.twist_half : nth;
   const Grp gp{tid, nth, 0};
   init_bars(gp, bar);
   const double *r2 = a.fac + it.r2off;
@@ -1108,15 +1091,15 @@ __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, A
   long long c = 0;
   for (int n_step = g.n_hi - 1; n_step >= g.n_lo; --n_step) {
     double *lin = ring ? g.lam_ring + (size_t)((n_step + 1 + g.jofs) % g.R) * Ntot : lam;
-    // mu[a][b] = lam[a][b] - lam[a][b+1] - lam[a+1][b] + lam[a+1][b+1] (class indices)
+    // mu[a][b] = lam[a][b] - lam[a][b+1] - lam[a+1][b] + lam[a+1][b+1] (class indices), stored reversed
     for (int e = tid; e < M * W; e += nth) {
       const int aa = e / W, cc = e - aa * W;
       const int sl = cc / Nz, b = cc - sl * Nz;
       const size_t o = (size_t)(it.s0 + sl) * slice + (size_t)(it.pr + 2 * aa) * n + it.pz + 2 * b;
-      Fa[aa * ld + cc] = lin[o] - lin[o + 2] - lin[o + 2 * n] + lin[o + 2 * n + 2];
+      Fa[(M - 1 - aa) * ld + sl * Nz + (Nz - 1 - b)] = lin[o] - lin[o + 2] - lin[o + 2 * n] + lin[o + 2 * n + 2];
     }
     __syncthreads();
-    adi_iterations<true, SMEM ? 2 : 8>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
+    adi_iterations<true, S_SMEM ? 2 : 8, TW>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
     // T1 = Lambda C02 on nsl * Nzfull columns: T1[a][b'] = sum_t Lambda[a][b' - t] C02[b' - t][t]
     for (int e = tid; e < M * Wf; e += nth) {
       const int aa = e / Wf, cc = e - aa * Wf;
@@ -1125,7 +1108,7 @@ __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, A
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
         const int b = bp - t;
-        if (b >= 0 && b < Nz) acc = fma(c02[b * C02STRIDE + t], S[aa * ld + sl * Nz + b], acc);
+        if (b >= 0 && b < Nz) acc = fma(c02[b * C02STRIDE + t], S[(M - 1 - aa) * ld + sl * Nz + (Nz - 1 - b)], acc);
       }
       Fa[aa * ld + cc] = acc;
     }
@@ -1402,24 +1385,34 @@ cudaError_t launch_sum_partials(const double *part, int n, double scale, double 
   return cudaGetLastError();
 }
 
-template <bool SMEM, int MAXT>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
 static cudaError_t launch_adjoint_t(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem,
                                     cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(adi_adjoint_kernel<SMEM, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adi_adjoint_kernel<SMEM, MAXT><<<a.nitems, threads, smem, st>>>(a, g);
+  adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW><<<a.nitems, threads, smem, st>>>(a, g);
   return cudaGetLastError();
 }
 
-// CTAs of at most 256 threads get the instantiation with the full register budget.
+template <bool S_SMEM, bool F_SMEM>
+static cudaError_t launch_adjoint_level(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem,
+                                        cudaStream_t st) {
+  if (a.twist_half > 0)     // twisted records: at most 2 x 128 threads
+    return threads <= 128 ? launch_adjoint_t<S_SMEM, F_SMEM, 128, true>(a, g, threads, smem, st)
+                          : launch_adjoint_t<S_SMEM, F_SMEM, 256, true>(a, g, threads, smem, st);
+  return threads <= 256 ? launch_adjoint_t<S_SMEM, F_SMEM, 256, false>(a, g, threads, smem, st)
+                        : launch_adjoint_t<S_SMEM, F_SMEM, 512, false>(a, g, threads, smem, st);
+}
+
+// Instantiations by work-array placement, as the forward kernel; CTAs of at
+// most 256 threads get the full register budget.
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || g.n_hi <= g.n_lo) return cudaSuccess;
-  if (a.use_smem == 2)
-    return threads <= 256 ? launch_adjoint_t<true, 256>(a, g, threads, smem, st)
-                          : launch_adjoint_t<true, 512>(a, g, threads, smem, st);
-  return threads <= 256 ? launch_adjoint_t<false, 256>(a, g, threads, smem, st)
-                        : launch_adjoint_t<false, 512>(a, g, threads, smem, st);
+  if (a.twist_half > 0 && threads > 256) return cudaErrorInvalidValue;
+  if (a.use_smem == 2) return launch_adjoint_level<true, true>(a, g, threads, smem, st);
+  if (a.use_smem == 1) return launch_adjoint_level<true, false>(a, g, threads, smem, st);
+  return launch_adjoint_level<false, false>(a, g, threads, smem, st);
 }
 
 template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>

@@ -24,7 +24,6 @@ struct AdiArgs {
   int ckpt_every;
   int m, n, p;
   int zero_other;          // write zeros into the non-solved radial parity rows
-  int transpose;           // 0: forward solve, 1: transposed (adjoint) solve
   double *gwork;           // global work arrays when the item does not fit in shared memory
   long long gwork_per_item;
   int use_smem;            // 2: S and Fa in shared memory, 1: S only, 0: neither

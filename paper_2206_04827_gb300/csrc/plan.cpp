@@ -369,13 +369,6 @@ Band HostPlan::Lblk(int k, int pr) const { return block(recomb(full_L(m, k)), pr
 Band HostPlan::Bblk(int pz) const { return block(recomb(full_C02(n)), pz); }
 Band HostPlan::D2blk(int pz) const { return block(recomb(op_D2(n)), pz); }
 
-static Band transpose(const Band &B) {
-  Band T(B.n, B.hi, B.lo);
-  for (int i = 0; i < B.n; ++i)
-    for (int j = std::max(0, i - B.lo); j <= std::min(B.n - 1, i + B.hi); ++j) T.at(j, i) = B.get(i, j);
-  return T;
-}
-
 // Pad a block band to fixed offsets [-lo, hi] (so kernels use fixed strides).
 static Band widen(const Band &B, int lo, int hi) {
   Band W(B.n, lo, hi);
@@ -401,6 +394,103 @@ void bdf_beta(int b, double beta[kMaxBdf]) {
                                                  {18.0 / 11.0, -9.0 / 11.0, 2.0 / 11.0, 0},
                                                  {48.0 / 25.0, -36.0 / 25.0, 16.0 / 25.0, -3.0 / 25.0}};
   for (int i = 0; i < kMaxBdf; ++i) beta[i] = (b >= 1 && b <= kMaxBdf) ? t[b][i] : 0.0;
+}
+
+// J T^T J (J the index reversal): the transpose read in reverse order, with the
+// band offsets of T itself.
+static Band flip_transpose(const Band &T) {
+  Band R(T.n, T.lo, T.hi);
+  for (int i = 0; i < T.n; ++i)
+    for (int j = std::max(0, i - T.lo); j <= std::min(T.n - 1, i + T.hi); ++j) R.at(i, j) = T.get(T.n - 1 - j, T.n - 1 - i);
+  return R;
+}
+
+// Radial records of Algorithm 1 (layout in plan.hpp) for the radial matrices
+// (A, Cm), band offsets -2 .. 3, shifts S, twisted split kr (0: one-sided).
+static std::string emit_radial(std::vector<double> &F, const Band &A, const Band &Cm, const Shifts &S, int M,
+                               int kr) {
+  for (int j = 0; j < S.J; ++j) {
+    const double pj = S.p[j], qj = S.q[j], s = qj - pj;
+    Band LU = axpby(1.0, A, -pj, Cm);
+    if (!lu_inplace(LU)) return "radial LU failed (zero pivot)";
+    Band UL;
+    if (kr) {
+      UL = axpby(1.0, A, -pj, Cm);
+      if (!ul_inplace(UL)) return "radial UL failed (zero pivot)";
+    }
+    for (int i = 0; i < M; ++i) {
+      for (int o = -2; o <= 3; ++o)
+        F.push_back((i + o >= 0 && i + o < M) ? (A.get(i, i + o) - qj * Cm.get(i, i + o)) / s : 0.0);
+      if (kr == 0 || i < kr) {            // LU row (top of a twisted solve)
+        F.push_back(i >= 1 ? -LU.get(i, i - 1) : 0.0);
+        F.push_back(i >= 2 ? -LU.get(i, i - 2) : 0.0);
+        const double dpiv = s / LU.get(i, i);
+        for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
+        F.push_back(dpiv);
+      } else if (i < kr + 3) {            // interface row: apply band only
+        for (int o = 0; o < 6; ++o) F.push_back(0.0);
+      } else {                            // UL row (bottom of a twisted solve)
+        for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -UL.get(i, i + o) : 0.0);
+        const double dpiv = s / UL.get(i, i);
+        F.push_back(-UL.get(i, i - 1) / s * dpiv);
+        F.push_back(-UL.get(i, i - 2) / s * dpiv);
+        F.push_back(dpiv);
+      }
+    }
+    if (kr) {                             // interface map (3 x 8), scaled by q - p
+      Band T = axpby(1.0, A, -pj, Cm);
+      std::vector<double> R;
+      if (!twist_interface(T, LU, UL, kr, 3, s, R)) return "radial interface solve failed";
+      F.insert(F.end(), R.begin(), R.end());
+    }
+  }
+  return std::string();
+}
+
+// Vertical records (layout in plan.hpp) for the vertical matrices (D, Bm),
+// band offsets -1 .. 2, shifts S, twisted split kz (0: one-sided).
+static std::string emit_vertical(std::vector<double> &F, const Band &D, const Band &Bm, const Shifts &S, int Nz,
+                                 int kz) {
+  for (int j = 0; j < S.J; ++j) {
+    Band T = axpby(1.0, D, S.q[j], Bm);
+    Band LU = T;
+    if (!lu_inplace(LU)) return "vertical LU failed (zero pivot)";
+    Band UL;
+    if (kz) {
+      UL = T;
+      if (!ul_inplace(UL)) return "vertical UL failed (zero pivot)";
+    }
+    const bool last = (j + 1 == S.J);
+    const double pn = last ? 0.0 : S.p[j + 1];
+    for (int cc = 0; cc < Nz; ++cc) {
+      if (kz == 0 || cc < kz) {           // LU column (top of a twisted solve)
+        const double dz = 1.0 / LU.get(cc, cc);
+        F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
+        F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
+        F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) * dz : 0.0);
+        F.push_back(dz);
+      } else if (cc < kz + 2) {           // interface column: apply band only
+        for (int o = 0; o < 4; ++o) F.push_back(0.0);
+      } else {                            // UL column (bottom of a twisted solve)
+        const double dz = 1.0 / UL.get(cc, cc);
+        F.push_back(cc + 1 < Nz ? -UL.get(cc, cc + 1) : 0.0);
+        F.push_back(cc + 2 < Nz ? -UL.get(cc, cc + 2) : 0.0);
+        F.push_back(-UL.get(cc, cc - 1) * dz);
+        F.push_back(dz);
+      }
+      for (int o = -1; o <= 2; ++o) {
+        const int l = cc + o;
+        F.push_back((!last && l >= 0 && l < Nz) ? D.get(cc, l) + pn * Bm.get(cc, l) : 0.0);
+      }
+    }
+    if (kz) {                             // interface map (3 x 5), padded to 16
+      std::vector<double> R;
+      if (!twist_interface(T, LU, UL, kz, 3, 1.0, R)) return "vertical interface solve failed";
+      F.insert(F.end(), R.begin(), R.end());
+      F.push_back(0.0);
+    }
+  }
+  return std::string();
 }
 
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
@@ -543,59 +633,17 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
         Band A = (kind >= 1) ? axpby(1.0, Cb[pr], -ka, L) : axpby(-1.0, L, 0.0, L);
         const long long roff = (long long)F.size();
         const int kr = (tw_ok && M >= kTwistMinM) ? (M - 3) / 2 : 0;   // twisted split of the radial solve
-        for (int j = 0; j < S.J; ++j) {
-          const double pj = S.p[j], qj = S.q[j], s = qj - pj;
-          Band LU = axpby(1.0, A, -pj, Cb[pr]);
-          if (!lu_inplace(LU)) return "radial LU failed (zero pivot)";
-          Band UL;
-          if (kr) {
-            UL = axpby(1.0, A, -pj, Cb[pr]);
-            if (!ul_inplace(UL)) return "radial UL failed (zero pivot)";
-          }
-          for (int i = 0; i < M; ++i) {
-            for (int o = -2; o <= 3; ++o)
-              F.push_back((i + o >= 0 && i + o < M) ? (A.get(i, i + o) - qj * Cb[pr].get(i, i + o)) / s : 0.0);
-            if (kr == 0 || i < kr) {            // LU row (top of a twisted solve)
-              F.push_back(i >= 1 ? -LU.get(i, i - 1) : 0.0);
-              F.push_back(i >= 2 ? -LU.get(i, i - 2) : 0.0);
-              const double dpiv = s / LU.get(i, i);
-              for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
-              F.push_back(dpiv);
-            } else if (i < kr + 3) {            // interface row: apply band only
-              for (int o = 0; o < 6; ++o) F.push_back(0.0);
-            } else {                            // UL row (bottom of a twisted solve)
-              for (int o = 1; o <= 3; ++o) F.push_back(i + o < M ? -UL.get(i, i + o) : 0.0);
-              const double dpiv = s / UL.get(i, i);
-              F.push_back(-UL.get(i, i - 1) / s * dpiv);
-              F.push_back(-UL.get(i, i - 2) / s * dpiv);
-              F.push_back(dpiv);
-            }
-          }
-          if (kr) {                             // interface map (3 x 8), scaled by q - p
-            Band T = axpby(1.0, A, -pj, Cb[pr]);
-            std::vector<double> R;
-            if (!twist_interface(T, LU, UL, kr, 3, s, R)) return "radial interface solve failed";
-            F.insert(F.end(), R.begin(), R.end());
-          }
-        }
-        // transposed radial factors (adjoint of the heat step)
+        std::string e = emit_radial(F, A, Cb[pr], S, M, kr);
+        if (!e.empty()) return e;
+        // adjoint (heat): the transposed system A^T X B + C^T X D = E is the forward-form system of the
+        // flipped transposes J A^T J, J C^T J, J B^T J, J D^T J on index-reversed arrays; its records
+        // have the forward layout (one-sided in cluster plans, whose adjoint runs one CTA per item)
         long long roffT = -1;
+        const int krT = (twist == 3) ? 0 : kr;
         if (kind >= 1) {
           roffT = (long long)F.size();
-          for (int j = 0; j < S.J; ++j) {
-            const double pj = S.p[j], qj = S.q[j], s = qj - pj;
-            Band LU = transpose(axpby(1.0, A, -pj, Cb[pr]));     // offsets -3 .. 2
-            if (!lu_inplace(LU)) return "transposed radial LU failed (zero pivot)";
-            for (int i = 0; i < M; ++i) {
-              for (int o = -3; o <= 2; ++o)
-                F.push_back((i + o >= 0 && i + o < M)
-                                ? (A.get(i + o, i) - qj * Cb[pr].get(i + o, i)) / s : 0.0);
-              for (int o = 1; o <= 3; ++o) F.push_back(i >= o ? -LU.get(i, i - o) : 0.0);
-              const double dpiv = s / LU.get(i, i);
-              for (int o = 1; o <= 2; ++o) F.push_back(i + o < M ? -LU.get(i, i + o) / s * dpiv : 0.0);
-              F.push_back(dpiv);
-            }
-          }
+          e = emit_radial(F, flip_transpose(A), flip_transpose(Cb[pr]), S, M, krT);
+          if (!e.empty()) return "transposed " + e;
         }
         // vertical factors per vertical parity; items
         for (int pz = 0; pz < 2; ++pz) {
@@ -604,65 +652,14 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
           Band D = axpby(-ka, D2b[pz], 0.0, D2b[pz]);
           const long long zoff = (long long)F.size();
           const int kz = (tw_ok && Nz >= kTwistMinN) ? (Nz - 2) / 2 : 0;   // twisted split of the vertical solve
-          for (int j = 0; j < S.J; ++j) {
-            Band T = axpby(1.0, D, S.q[j], Bb[pz]);
-            Band LU = T;
-            if (!lu_inplace(LU)) return "vertical LU failed (zero pivot)";
-            Band UL;
-            if (kz) {
-              UL = T;
-              if (!ul_inplace(UL)) return "vertical UL failed (zero pivot)";
-            }
-            const bool last = (j + 1 == S.J);
-            const double pn = last ? 0.0 : S.p[j + 1];
-            for (int cc = 0; cc < Nz; ++cc) {
-              if (kz == 0 || cc < kz) {         // LU column (top of a twisted solve)
-                const double dz = 1.0 / LU.get(cc, cc);
-                F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
-                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
-                F.push_back(cc + 2 < Nz ? -LU.get(cc, cc + 2) * dz : 0.0);
-                F.push_back(dz);
-              } else if (cc < kz + 2) {         // interface column: apply band only
-                for (int o = 0; o < 4; ++o) F.push_back(0.0);
-              } else {                          // UL column (bottom of a twisted solve)
-                const double dz = 1.0 / UL.get(cc, cc);
-                F.push_back(cc + 1 < Nz ? -UL.get(cc, cc + 1) : 0.0);
-                F.push_back(cc + 2 < Nz ? -UL.get(cc, cc + 2) : 0.0);
-                F.push_back(-UL.get(cc, cc - 1) * dz);
-                F.push_back(dz);
-              }
-              for (int o = -1; o <= 2; ++o) {
-                const int l = cc + o;
-                F.push_back((!last && l >= 0 && l < Nz) ? D.get(cc, l) + pn * Bb[pz].get(cc, l) : 0.0);
-              }
-            }
-            if (kz) {                           // interface map (3 x 5), padded to 16
-              std::vector<double> R;
-              if (!twist_interface(T, LU, UL, kz, 3, 1.0, R)) return "vertical interface solve failed";
-              F.insert(F.end(), R.begin(), R.end());
-              F.push_back(0.0);
-            }
-          }
+          std::string ev = emit_vertical(F, D, Bb[pz], S, Nz, kz);
+          if (!ev.empty()) return ev;
           long long zoffT = -1;
+          const int kzT = (twist == 3) ? 0 : kz;
           if (kind >= 1) {
             zoffT = (long long)F.size();
-            for (int j = 0; j < S.J; ++j) {
-              Band LU = transpose(axpby(1.0, D, S.q[j], Bb[pz]));   // offsets -2 .. 1
-              if (!lu_inplace(LU)) return "transposed vertical LU failed (zero pivot)";
-              const bool last = (j + 1 == S.J);
-              const double pn = last ? 0.0 : S.p[j + 1];
-              for (int cc = 0; cc < Nz; ++cc) {
-                const double dz = 1.0 / LU.get(cc, cc);
-                F.push_back(cc >= 1 ? -LU.get(cc, cc - 1) : 0.0);
-                F.push_back(cc >= 2 ? -LU.get(cc, cc - 2) : 0.0);
-                F.push_back(cc + 1 < Nz ? -LU.get(cc, cc + 1) * dz : 0.0);
-                F.push_back(dz);
-                for (int o = -2; o <= 1; ++o) {
-                  const int l = cc + o;
-                  F.push_back((!last && l >= 0 && l < Nz) ? D.get(l, cc) + pn * Bb[pz].get(l, cc) : 0.0);
-                }
-              }
-            }
+            ev = emit_vertical(F, flip_transpose(D), flip_transpose(Bb[pz]), S, Nz, kzT);
+            if (!ev.empty()) return "transposed " + ev;
           }
           // one item per slice group
           auto add_item = [&](int s0, int nsl) {
@@ -673,7 +670,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
             it.roffT = roffT; it.zoffT = zoffT;
             it.m = m; it.n = n; it.xoff = 0;
             it.lkoff = lkoff[k * 2 + pr]; it.d2off = d2off[pz];
-            it.twr = kr; it.twz = kz;
+            it.twr = kr; it.twz = kz; it.twrT = krT; it.twzT = kzT;
             KT.items.push_back(it);
           };
           if (k == 0) add_item(0, 1);

@@ -35,11 +35,11 @@ struct Band {
 // so that Z_i = [11] * y_i + [10] Z_{i+3} + [9] Z_{i+2} + [8] Z_{i+1}: the loop-carried
 // recurrence is a single fused multiply-add per row.
 constexpr int RSTRIDE = 12;
-// The transposed system (adjoint) uses the same record sizes with the band
-// orientations swapped: radial [0..5] (A - qC)^T[i][i+o]/(q-p), o = -3 .. 2;
-// [6..8] -L[i][i-1..i-3]; [9..10] -U[i][i+1..i+2]/U[i][i]; [11] (q-p)/U[i][i],
-// where L U is the no-pivot LU of (A - pC)^T.  Vertical: [0..1] -L[c][c-1..c-2];
-// [2] -U[c][c+1]/U[c][c]; [3] 1/U[c][c]; [4..7] (D + p'B)^T[c][c+o], o = -2 .. 1.
+// The transposed system of the adjoint, A^T X B + C^T X D = E, equals the
+// forward-form system of the flipped transposes J A^T J, J C^T J, J B^T J,
+// J D^T J (J the index reversal, which keeps the band offsets) on
+// index-reversed arrays; its records have exactly the forward layout below,
+// built from those matrices with the same shifts.
 // Factors per column of one vertical matrix (D + qB) and the next apply band:
 //   [0]     -L[c][c-1]
 //   [1..2]  -U[c][c+1] / U[c][c], -U[c][c+2] / U[c][c]   (pivot folded in)
@@ -89,6 +89,7 @@ struct Item {
   long long lkoff;    // radial operator L_k bands [M][3] (lifting of boundary data)
   long long d2off;    // vertical D2 band [Nz] (lifting of boundary data)
   int twr, twz;       // twisted split rows of the radial / vertical solves (0: plain)
+  int twrT, twzT;     // the same for the transposed (adjoint) records
 };
 
 struct Shifts {

@@ -272,8 +272,8 @@ class Plan:
         tr = int(bool(transposed))
         _check(_lib.cyl_plan_item_tables(self._h, which, item, j, tr, info, None, None), 'cyl_plan_item_tables')
         M, Nz, J, twr, twz = info[0], info[1], info[2], info[3], info[4]
-        rad = (ctypes.c_double * (M * 12 + (24 if twr and not tr else 0)))()
-        ver = (ctypes.c_double * (Nz * 8 + (16 if twz and not tr else 0)))()
+        rad = (ctypes.c_double * (M * 12 + (24 if twr else 0)))()
+        ver = (ctypes.c_double * (Nz * 8 + (16 if twz else 0)))()
         _check(_lib.cyl_plan_item_tables(self._h, which, item, j, tr, info, rad, ver), 'cyl_plan_item_tables')
         keys = ('M', 'Nz', 'J', 'twr', 'twz', 'k', 'pr', 'pz')
         return dict(zip(keys, list(info))), np.array(rad), np.array(ver)

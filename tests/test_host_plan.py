@@ -349,76 +349,49 @@ def test_batch_configuration_on_host(cyl):
         tw.heat_step(x, None, 1)
 
 
-def _radial_column_T(rec, U, f, first):
-    """One column of the transposed radial sweep (apply offsets -3..2, L
-    bandwidth 3, U bandwidth 2)."""
-    M = len(f)
-    y = f.copy()
-    if not first:
-        for i in range(M):
-            for o in range(-3, 3):
-                if 0 <= i + o < M:
-                    y[i] += rec[i, o + 3] * U[i + o]
-    w = np.zeros(M)
-    for i in range(M):
-        w[i] = y[i] + sum(rec[i, 5 + d] * w[i - d] for d in (1, 2, 3) if i - d >= 0)
-    z = np.zeros(M + 2)
-    for i in range(M - 1, -1, -1):
-        z[i] = rec[i, 11] * w[i] + rec[i, 9] * z[i + 1] + rec[i, 10] * z[i + 2]
-    return z[:M]
-
-
-def _vertical_row_T(rec, zrow):
-    Nz = len(zrow)
-    w = np.zeros(Nz)
-    for c in range(Nz):
-        w[c] = zrow[c] + sum(rec[c, d - 1] * w[c - d] for d in (1, 2) if c - d >= 0)
-    x = np.zeros(Nz + 1)
-    for c in range(Nz - 1, -1, -1):
-        x[c] = rec[c, 3] * w[c] + rec[c, 2] * x[c + 1]
-    x = x[:Nz]
-    u = np.zeros(Nz)
-    for c in range(Nz):
-        for o in range(-2, 2):
-            if 0 <= c + o < Nz:
-                u[c] += rec[c, 6 + o] * x[c + o]
-    return x, u
-
-
-@pytest.mark.parametrize('which', [1, 3])
-def test_transposed_item_tables_drive_adi_to_the_direct_solve(cyl, which):
-    """The adjoint's records (the transposed system A^T X B + C^T X D = E with
-    the same shifts) drive Algorithm 1 to the direct solution of that system,
-    for the BDF1 and the BDF3 step."""
+@pytest.mark.parametrize('which,flags', [(1, 0), (3, 0), (1, 'cluster')])
+def test_transposed_item_tables_drive_adi_to_the_direct_solve(cyl, which, flags):
+    """The adjoint's records -- the forward-layout records of the flipped
+    transposes J A^T J, J C^T J, J B^T J, J D^T J, twisted where the forward
+    records are (one-sided in cluster plans) -- drive Algorithm 1, run on the
+    index-reversed right side, to the direct solution of the transposed
+    system A^T X B + C^T X D = E with the same shifts, for the BDF1 and the
+    BDF3 step."""
     m, n, p = 30, 26, 8
-    plan = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=False, heat=True, host_only=True, bdf_order=3)
+    extra = cyl.FORCE_CLUSTER if flags == 'cluster' else 0
+    plan = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=False, heat=True, host_only=True, bdf_order=3,
+                    extra_flags=extra)
     rng = np.random.default_rng(21 + which)
     item = 0
-    checked = 0
+    checked = twisted = 0
     while True:
         try:
             info, _, _ = plan.item_tables(which, item, 0, transposed=True)
         except cyl.CylError:
             break
         if item % 3 == 0:
-            M, Nz, J = info['M'], info['Nz'], info['J']
+            M, Nz, J, kr, kz = info['M'], info['Nz'], info['J'], info['twr'], info['twz']
+            twisted += bool(kr and kz)
             A, C = plan.operator(0, which, info['k'], info['pr']), plan.operator(1, which, info['k'], info['pr'])
             B, D = plan.operator(2, which, info['k'], info['pz']), plan.operator(3, which, info['k'], info['pz'])
             ii, jj = np.meshgrid(np.arange(M), np.arange(Nz), indexing='ij')
             E = rng.standard_normal((M, Nz)) * 1.3 ** (-(ii + jj))
+            Er = E[::-1, ::-1].copy()
             U = np.zeros((M, Nz))
             for j in range(J):
                 _, rad, ver = plan.item_tables(which, item, j, transposed=True)
-                rrec, vrec = rad.reshape(M, 12), ver.reshape(Nz, 8)
-                Z = np.stack([_radial_column_T(rrec, U[:, c], E[:, c], j == 0) for c in range(Nz)], axis=1)
-                rows = [_vertical_row_T(vrec, Z[a]) for a in range(M)]
+                rrec, Rr = rad[:M * 12].reshape(M, 12), rad[M * 12:]
+                vrec, Rz = ver[:Nz * 8].reshape(Nz, 8), ver[Nz * 8:]
+                Z = np.stack([_radial_column(rrec, Rr, U[:, c], Er[:, c], j == 0, kr) for c in range(Nz)], axis=1)
+                rows = [_vertical_row(vrec, Rz, Z[a], kz) for a in range(M)]
                 X = np.stack([r[0] for r in rows])
                 U = np.stack([r[1] for r in rows])
             Xd = sy.solve_kron(A.T, B.T, C.T, D.T, E)
-            assert np.abs(X - Xd).max() < 1e-11 * np.abs(Xd).max(), item
+            assert np.abs(X[::-1, ::-1] - Xd).max() < 1e-11 * np.abs(Xd).max(), item
             checked += 1
         item += 1
     assert checked >= 3
+    assert (twisted == 0) if flags == 'cluster' else (twisted == checked)
     with pytest.raises(cyl.CylError) as ei:
         cyl.Plan(m, n, p, host_only=True).item_tables(0, 0, 0, transposed=True)
     assert ei.value.status == cyl.ESTATE
