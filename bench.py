@@ -22,6 +22,10 @@ Other workloads (same JSON line, for the other problem sizes of the method):
               forward run + adjoint (gradients in T0, space-time g, alpha)
   heat128_bdf4  the 128^3 heat problem under BDF 4 (100 steps from T0 alone:
               the first three steps start up through BDF 1-3)
+  xform128, xform512  value -> coefficient -> value round trip of a 128^3 /
+              512^3 field (the Section 2 transforms alone)
+  ns128       10 Navier-Stokes steps (Section 4, poloidal-toroidal form, IMEX
+              BDF1) on 128^3, Re 100, dt 1e-3
 
 Legs: --impl ours (default) times the CUDA path through the C ABI; --impl
 reference times the FP64 CPU oracle on the host cores on a bounded sample of
@@ -448,15 +452,18 @@ class Large512(Workload):
     TRAFFIC = (102546660096 + 88557331456 + 1747276132864 + 1472403574784, None)
     TRAFFIC_BASIS = 'ncu capture of the bench step (two launches)'
 
-    def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None):
-        m = n = p = L512
+    def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None, n_theta=L512):
+        m = n = L512
+        p = n_theta                  # 512 = the workload; fewer only for profiling
         self.torch, self.cyl = torch, cyl
         # ADI tolerance 1e-15: at 1e-14 the 20-step run ends at 1.7e-12 of the (refined) oracle, the
         # Zolotarev bound being optimistic for the non-normal 512-point pencils
         self.plan = cyl.Plan(m, n, p, ALPHA_512, DT_512, TOL_512, poisson=True, heat=True,
                              stream=stream.cuda_stream)
-        if f_host is None:
+        if f_host is None or p != L512:
             f_host = inputs.smooth_coeffs(p, m, n, 1.1, inputs.rng_for(SEED_512))
+        if p != L512:
+            self.TRAFFIC = None
         self.f = torch.as_tensor(f_host, device=dev)
         self.T = torch.empty_like(self.f)
         self.hsteps = HSTEPS_512
@@ -465,7 +472,8 @@ class Large512(Workload):
         self.launches = 2
         self.kernel = 'adi_kernel'
         self.config = {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
-                                   'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out',
+                                   'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out'
+                                   + ('' if p == L512 else ' [PROFILING CASE: n_theta = %d]' % p),
                        'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL_512,
                        'time_steps_per_bench_step': 1 + self.hsteps,
                        'l2': 'inputs larger than L2 (1.07 GB per field)'}
@@ -479,6 +487,8 @@ class Large512(Workload):
         """The last timed step's final state and a fresh Poisson solve, on the
         sampled slices and coefficients of the oracle's stored 512^3 values."""
         t = self.torch
+        if self.f.shape[0] != L512:
+            return {}
         ref = np.load(GOLD512)
         sl = t.as_tensor(ref['slices'], device=self.T.device)
         idx = t.as_tensor(ref['idx'], device=self.T.device)
@@ -690,8 +700,107 @@ class Heat128Bdf4(Heat128):
         outh.copy_(self.H[0], non_blocking=True)
 
 
+class Xform(Workload):
+    """Value -> coefficient -> value round trip (Section 2 transforms) of an
+    L^3 field: one bench step = both directions; units = N per step."""
+    L = 128
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        L = self.L
+        self.name = 'xform%d' % L
+        self.plan = cyl.Plan(L, L, L, stream=stream.cuda_stream)
+        self.v = torch.as_tensor(np.random.default_rng(5).standard_normal((L, L, L)), device=dev)
+        self.c = torch.empty_like(self.v)
+        self.units = L ** 3
+        info, _ = cyl.xform_table(0, L)
+        P = info['P']
+        # FP64 flops of the chirp-z transforms (FMA = 2): per complex line two radix-2 FFTs of
+        # 5 P log2 P flops (10 per butterfly) and three complex products per point (pre, kernel
+        # spectrum, post: 12 P); per direction L^2 lines in r, L^2 in z and L^2 / 2 theta line pairs
+        per_line = 10 * P * info['logP'] + 12 * P
+        self.flops = 2 * per_line * (2 * L * L + L * L / 2.0)
+        self.launches = 6
+        self.kernel = 'chirp_xform_kernel'
+        self.config = {'workload': 'value <-> coefficient round trip of a %d^3 field (chirp-z DCT-I in r, z; DFT '
+                                   'in theta)' % L, 'n_r': L, 'n_z': L, 'n_theta': L,
+                       'l2': 'inputs larger than L2' if 8 * L ** 3 > 129e6 else 'flushed between timed steps (256 MB write)'}
+        self.host = None
+
+    def step(self):
+        self.plan.vals2coeffs(self.v, self.c)
+        self.plan.coeffs2vals(self.c, self.v)
+
+    def e2e_setup(self):
+        t = __import__('torch')
+        self.host = (self.v.cpu().pin_memory(), t.empty(self.v.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        vh, oh = self.host
+        self.v.copy_(vh, non_blocking=True)
+        self.step()
+        oh.copy_(self.v, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.host[0].numel() * 8, self.host[1].numel() * 8
+
+
+class Xform512(Xform):
+    L = 512
+
+
+class NS128(Workload):
+    """Navier-Stokes steps (Section 4, poloidal-toroidal form, IMEX BDF1) on
+    128^3: Re = 100, dt = 1e-3, 10 steps per bench step from a smooth seeded
+    vorticity state (decay 1.25)."""
+    name = 'ns128'
+    STEPS = 10
+
+    def __init__(self, cyl, torch, dev, stream, nsteps):
+        L = 128
+        self.torch = torch
+        self.plan = cyl.Plan(L, L, L, 1.0 / 100.0, 1e-3, TOL, poisson=True, heat=True, extra_flags=cyl.WITH_DISK,
+                             stream=stream.cuda_stream)
+        rng = inputs.rng_for(1005)
+        self.L0 = torch.as_tensor(inputs.smooth_coeffs(L, L, L, 1.25, rng), device=dev)
+        self.G0 = torch.as_tensor(inputs.smooth_coeffs(L, L, L, 1.25, rng), device=dev)
+        self.Lw, self.Gw = torch.empty_like(self.L0), torch.empty_like(self.G0)
+        self.ws = torch.empty((self.plan.ns_workspace_bytes() + 7) // 8, dtype=torch.float64, device=dev)
+        self.units = L ** 3 * self.STEPS
+        # the ADI solves of a step: one Poisson solve and two heat steps
+        self.flops = self.STEPS * (self.plan.flops(0, 1) + 2 * self.plan.flops(1, 1))
+        self.launches = self.STEPS * 150
+        self.kernel = 'adi_kernel + chirp_xform_kernel'
+        self.config = {'workload': 'Navier-Stokes 128^3 (poloidal-toroidal vorticity, IMEX BDF1), Re 100, dt 1e-3, '
+                                   '%d steps from smooth seeded potentials' % self.STEPS,
+                       'n_r': L, 'n_z': L, 'n_theta': L, 'l2': 'flushed between timed steps (256 MB write)'}
+        self.host = None
+
+    def reset(self):
+        self.Lw.copy_(self.L0)
+        self.Gw.copy_(self.G0)
+
+    def step(self):
+        self.plan.ns_step(self.Lw, self.Gw, self.STEPS, workspace=self.ws)
+
+    def e2e_setup(self):
+        t = self.torch
+        self.host = (self.L0.cpu().pin_memory(), self.G0.cpu().pin_memory(),
+                     t.empty(self.L0.shape, dtype=t.float64).pin_memory())
+
+    def e2e_step(self):
+        lh, gh, oh = self.host
+        self.Lw.copy_(lh, non_blocking=True)
+        self.Gw.copy_(gh, non_blocking=True)
+        self.step()
+        oh.copy_(self.Lw, non_blocking=True)
+
+    def e2e_bytes(self):
+        return 2 * self.host[0].numel() * 8, self.host[2].numel() * 8
+
+
 WORKLOADS = {'large512': Large512, 'heat128': Heat128, 'poisson33': Poisson33, 'batch256': Batch256,
-             'adjoint128': Adjoint128, 'heat128_bdf4': Heat128Bdf4}
+             'adjoint128': Adjoint128, 'heat128_bdf4': Heat128Bdf4, 'xform128': Xform, 'xform512': Xform512,
+             'ns128': NS128}
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -710,9 +819,9 @@ def run_ours(args):
 
     # CPU baseline first (the pool is spawned; the sample runs before heavy GPU use)
     cpu, cpu_res, f512 = None, None, None
-    if args.workload == 'large512':
+    if args.workload == 'large512' and args.n_theta == L512:
         f512 = inputs.smooth_coeffs(L512, L512, L512, 1.1, inputs.rng_for(SEED_512))
-    if rank == 0 and not args.no_cpu_baseline and args.workload in CPU_LEGS:
+    if rank == 0 and not args.no_cpu_baseline and args.workload in CPU_LEGS and args.n_theta == L512:
         cpu = OracleSampler(args.workload, args.cpu_slices, args.cpu_steps, f512=f512)
         cpu_res = cpu.run()
         cpu.close()
@@ -720,7 +829,7 @@ def run_ours(args):
     from paper_2206_04827_gb300 import cyl
     stream = torch.cuda.current_stream(dev)
     if args.workload == 'large512':
-        wl = Large512(cyl, torch, dev, stream, args.nsteps, f_host=f512)
+        wl = Large512(cyl, torch, dev, stream, args.nsteps, f_host=f512, n_theta=args.n_theta)
     else:
         wl = WORKLOADS[args.workload](cyl, torch, dev, stream, args.nsteps)
     f512 = None
@@ -856,6 +965,8 @@ def main():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--batch-problems', type=int, default=256,
                     help='problems of the batch256 workload (256 = the workload; fewer only for profiling)')
+    ap.add_argument('--n-theta', type=int, default=L512,
+                    help='n_theta of the large512 workload (512 = the workload; fewer only for profiling)')
     ap.add_argument('--nsteps', type=int, default=NSTEPS,
                     help='BDF1 steps per bench step of heat128 (100 = the workload; fewer only for profiling)')
     args = ap.parse_args()

@@ -75,12 +75,12 @@ typedef enum {
 #define CYL_PLAIN_SWEEPS 128u
 /* build the horizontal (disk) Poisson tables for cyl_disk_poisson */
 #define CYL_WITH_DISK    256u
-/* cluster mode on any grid (for tests).  Without the flag a plan uses it
- * where one work item's iterate does not fit an SM's shared memory (about
- * 220 points per axis and more): the CTAs of a thread-block cluster then
- * share each item through its global work area, each with at most 128
- * chains per sweep, solved as twisted two-thread chains.  CYL_FORCE_GLOBAL
- * or CYL_PLAIN_SWEEPS turn cluster mode off. */
+/* cluster mode: the CTAs of a thread-block cluster share each work item
+ * through its global work area, each with at most 128 chains per sweep,
+ * solved as twisted two-thread chains (at most 8 CTAs per item: grids up
+ * to about 1024 points per axis).  Off by default: on GB300 it is slower
+ * than one CTA per item for the grids whose work arrays leave shared memory.
+ * CYL_FORCE_GLOBAL or CYL_PLAIN_SWEEPS override it. */
 #define CYL_FORCE_CLUSTER 512u
 
 /* space selector of cyl_poisson */
@@ -397,6 +397,36 @@ cyl_status cyl_sync(cyl_plan_t plan);
 #define CYL_NOALLOC_SCRATCH_DOUBLES (1 << 23)
 cyl_status cyl_vals2coeffs_noalloc(int n_r, int n_z, int n_theta, const double *vals, double *coeffs,
                                    void *stream);
+
+/*
+ * cyl_ns_step -- nsteps time steps of the incompressible Navier-Stokes
+ * equations in vorticity form (Section 4, eq. ns) on the poloidal-toroidal
+ * (PT) decomposition (eq. pt) of the vorticity, omega = curl(lam_w z) +
+ * curl curl(gam_w z), Re = 1 / alpha of the plan.  Each step: lambda_v =
+ * gam_w and -lap gamma_v = lam_w (eq. ptcurl, one Poisson solve); v and
+ * omega on the grid (eq. pt; derivatives on coefficients, the factors 1/r on
+ * grid values); N = v x omega pointwise; the PT decomposition (lambda_a,
+ * gamma_a) of curl N from eq. ptpoisson (right sides z . curl N and
+ * z . curl curl N, two horizontal Poisson solves); then eq. NSrewrite by the
+ * first-order implicit-explicit BDF: one BDF1 heat step each for lam_w and
+ * gam_w with forcing lambda_a, gamma_a.  Boundary data (reading of the
+ * unstated no-slip conditions): homogeneous Dirichlet in every scalar solve
+ * (gamma_v on the whole wall, gamma_a and lambda_a at r = +-1, lam_w, gam_w
+ * on the whole wall).
+ *
+ *   plan       from cyl_plan with CYL_WITH_POISSON | CYL_WITH_HEAT |
+ *              CYL_WITH_DISK, alpha = 1 / Re, dt the step; n_r even (no grid
+ *              point on the axis, where the factors 1/r are applied).
+ *   lam_w, gam_w  device coefficient arrays of N float64 (in / out).
+ *   workspace  caller-owned device memory of cyl_ns_workspace bytes.
+ *
+ * CYL_ESTATE when the plan lacks one of the three solvers, CYL_EINVAL for an
+ * odd n_r, a short workspace or NULL pointers.  Asynchronous on the plan's
+ * stream; allocates nothing.
+ */
+cyl_status cyl_ns_workspace(cyl_plan_t plan, size_t *bytes);
+cyl_status cyl_ns_step(cyl_plan_t plan, double *lam_w, double *gam_w, int nsteps, void *workspace,
+                       size_t workspace_bytes);
 
 /*
  * cyl_xform_table -- host copy of the table block of one chirp-z line

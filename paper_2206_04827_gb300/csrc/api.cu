@@ -37,6 +37,7 @@ struct cyl_plan_s {
   cyl::XformDesc xd[6];
   long long xoff[6] = {};
   double *d_xtab = nullptr;
+  double *d_radius = nullptr;   // radial grid points r_j (Definition "grid"), Navier-Stokes step
   int sms = 152;
   double *d_tmp[3] = {};        // N-element scratch arrays
   // batch plans (cyl_plan_batch): several problems, two persistent launch classes
@@ -100,6 +101,7 @@ void free_device(cyl_plan_s *P) {
   for (auto &p : P->d_items) cudaFree(p);
   cudaFree(P->d_gwork);
   cudaFree(P->d_xtab);
+  cudaFree(P->d_radius);
   for (auto &p : P->d_tmp) cudaFree(p);
   cudaFree(P->d_err);
   cudaFree(P->d_apart);
@@ -387,19 +389,19 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
   if ((flags & CYL_WITH_HEAT) && !(alpha > 0.0 && dt > 0.0)) return CYL_EINVAL;
   if (bdf_order < 1 || bdf_order > cyl::kMaxBdf) return CYL_EINVAL;
   if ((long long)n_r * n_z * n_theta > (1LL << 40)) return CYL_EINVAL;
-  // Cluster mode where one item's iterate S would not fit shared memory (its sizes follow from the
-  // grid: class rows (n_r + 1) / 2, class columns per slice (n_z + 1) / 2, two slices per item when
-  // n_theta >= 4): C CTAs per item, each with at most kTwistMaxChains chains per sweep.
+  // Cluster mode (CYL_FORCE_CLUSTER): C CTAs per item, each with at most kTwistMaxChains chains per
+  // sweep (two slices per item when n_theta >= 4, class sizes (n_r - 1) / 2 and (n_z - 1) / 2).
+  // Measured on GB300 at 512^2 x 256 it reaches 0.44 of the FP64 peak against 0.59 for one CTA per
+  // item with the work arrays in global memory (the twisted sweeps' registers allow one 256-thread
+  // CTA per SM, too few warps to hide the L2 latency of the shared work arrays), so it is not the
+  // default for any grid.
   int cluster = 0;
-  {
+  if ((flags & CYL_FORCE_CLUSTER) && !(flags & (CYL_FORCE_GLOBAL | CYL_PLAIN_SWEEPS))) {
     const int maxM = std::max(0, (n_r - 1) / 2), maxNz = std::max(0, (n_z - 1) / 2);
-    const int rows = (n_r + 1) / 2, nsl = n_theta >= 4 ? 2 : 1;
-    const int ld = (nsl * ((n_z + 1) / 2)) | 1;
-    const bool s_fits = cyl::adi_smem_bytes(ld, rows, maxM, maxNz, 1, 0) <= kSmemLimit;
+    const int nsl = n_theta >= 4 ? 2 : 1;
     const int chains = nsl * std::max(maxM, maxNz);
     const int C = std::max(2, (chains + cyl::kTwistMaxChains - 1) / cyl::kTwistMaxChains);
-    if (!(flags & (CYL_FORCE_GLOBAL | CYL_PLAIN_SWEEPS)) && ((flags & CYL_FORCE_CLUSTER) || !s_fits) && C <= 8)
-      cluster = C;
+    if (C <= 8) cluster = C;
   }
   cyl_plan_s *P = new (std::nothrow) cyl_plan_s();
   if (!P) return CYL_ENOMEM;
@@ -486,6 +488,11 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
       if (xt.size() & 1) xt.push_back(0.0);          // keep every block 16-byte aligned
     }
     e = upload(&P->d_xtab, xt.data(), xt.size());
+  }
+  if (e == cudaSuccess) {
+    std::vector<double> rad(n_r);
+    for (int j = 0; j < n_r; ++j) rad[j] = std::cos((n_r - 1 - j) * 3.14159265358979323846 / (n_r - 1));
+    e = upload(&P->d_radius, rad.data(), rad.size());
   }
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc((void **)&P->d_tmp[i], P->N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void **)&P->d_err, sizeof(int));
@@ -1001,6 +1008,136 @@ cyl_status cyl_plan_operator(cyl_plan_t P, int op, int which, int k, int parity,
   if (out)
     for (int i = 0; i < B.n; ++i)
       for (int j = 0; j < B.n; ++j) out[(size_t)i * B.n + j] = B.get(i, j);
+  return CYL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kNsArrays = 12;   // workspace arrays of N doubles of cyl_ns_step
+
+// One Navier-Stokes step (Section 4) on the vorticity PT state (lw, gw); see
+// include/cyl.h: cyl_ns_step.  W[0] gamma_v; W[1..3] v, then N = v x omega
+// (grid values); W[4..6] omega values, then N's coefficients; W[7], W[8]
+// coefficient scratch; W[9] value scratch; W[10], W[11] s1 / s2, then
+// gamma_a / lambda_a.
+cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kNsArrays]) {
+  const HostPlan &h = P->hp;
+  const int m = h.m, n = h.n, p = h.p;
+  const long long mn = (long long)m * n, N = (long long)p * mn;
+  const int sms = P->sms;
+  cudaStream_t st = P->st;
+  cyl_status s;
+  cudaError_t e = cudaSuccess;
+  // derivative of coefficients `in` into `out`: 'r', 'z' or 't' (theta)
+  auto d = [&](char ax, const double *in, double *out) -> cudaError_t {
+    if (ax == 't') return cyl::launch_deriv_theta(in, out, p, mn, sms, st);
+    if (ax == 'r') return cyl::launch_deriv_cheb(in, out, p, m, n, sms, st);
+    return cyl::launch_deriv_cheb(in, out, (long long)p * m, n, 1, sms, st);
+  };
+  // dst (grid values) (+)= coef r^rpow values(C)
+  auto acc = [&](double *dst, const double *C, double coef, int rpow, bool init) -> cyl_status {
+    cyl_status q = coeffs2vals_impl(P, C, W[9]);
+    if (q != CYL_OK) return q;
+    return from_cuda(cyl::launch_accum_r(dst, W[9], P->d_radius, p, m, n, coef, rpow, init, sms, st));
+  };
+#define NS_TRY(x) do { if ((e = (x)) != cudaSuccess) return from_cuda(e); } while (0)
+#define NS_S(x) do { if ((s = (x)) != CYL_OK) return s; } while (0)
+  // PT components of curl(lam z) + curl curl(gam z) into (Vr, Vt, Vz), grid values (eq. pt)
+  auto pt_field = [&](const double *lam, const double *gam, double *Vr, double *Vt, double *Vz) -> cyl_status {
+    cyl_status q;
+    cudaError_t ee;
+    if ((ee = d('t', lam, W[7])) != cudaSuccess) return from_cuda(ee);          // V_r = r^-1 d_th lam + d_r d_z gam
+    if ((q = acc(Vr, W[7], 1.0, -1, true)) != CYL_OK) return q;
+    if ((ee = d('z', gam, W[7])) != cudaSuccess || (ee = d('r', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
+    if ((q = acc(Vr, W[8], 1.0, 0, false)) != CYL_OK) return q;
+    if ((ee = d('r', lam, W[7])) != cudaSuccess) return from_cuda(ee);          // V_th = -d_r lam + r^-1 d_th d_z gam
+    if ((q = acc(Vt, W[7], -1.0, 0, true)) != CYL_OK) return q;
+    if ((ee = d('z', gam, W[7])) != cudaSuccess || (ee = d('t', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
+    if ((q = acc(Vt, W[8], 1.0, -1, false)) != CYL_OK) return q;
+    if ((ee = d('r', gam, W[7])) != cudaSuccess || (ee = d('r', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
+    if ((q = acc(Vz, W[8], -1.0, 0, true)) != CYL_OK) return q;                 // V_z = -Delta_h gam
+    if ((q = acc(Vz, W[7], -1.0, -1, false)) != CYL_OK) return q;
+    if ((ee = d('t', gam, W[7])) != cudaSuccess || (ee = d('t', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
+    return acc(Vz, W[8], -1.0, -2, false);
+  };
+  // 1. velocity potentials (eq. ptcurl): lambda_v = gamma_w, -lap gamma_v = lambda_w
+  NS_S(run_adi(P, 0, lw, W[0], nullptr, 0.0, 0, 1, nullptr, 1));
+  // 2. v and omega on the grid (eq. pt)
+  NS_S(pt_field(gw, W[0], W[1], W[2], W[3]));
+  NS_S(pt_field(lw, gw, W[4], W[5], W[6]));
+  // 3. N = v x omega (in place of v)
+  {
+    const double *V[3] = {W[1], W[2], W[3]}, *Om[3] = {W[4], W[5], W[6]};
+    double *No[3] = {W[1], W[2], W[3]};
+    NS_TRY(cyl::launch_cross(V, Om, No, N, sms, st));
+  }
+  for (int c = 0; c < 3; ++c) NS_S(vals2coeffs_impl(P, W[1 + c], W[4 + c]));
+  // 4. right sides of eq. ptpoisson for a = curl N:
+  //    s1 = d_r N_th + N_th / r - r^-1 d_th N_r
+  NS_TRY(d('r', W[5], W[7]));
+  NS_S(acc(W[10], W[7], 1.0, 0, true));
+  NS_TRY(cyl::launch_accum_r(W[10], W[2], P->d_radius, p, m, n, 1.0, -1, false, sms, st));
+  NS_TRY(d('t', W[4], W[7]));
+  NS_S(acc(W[10], W[7], -1.0, -1, false));
+  NS_S(vals2coeffs_impl(P, W[10], W[10]));
+  //    s2 = d_z (d_r N_r + N_r / r + r^-1 d_th N_th) - Delta_h N_z
+  NS_TRY(d('r', W[4], W[7]));
+  NS_S(acc(W[11], W[7], 1.0, 0, true));
+  NS_TRY(cyl::launch_accum_r(W[11], W[1], P->d_radius, p, m, n, 1.0, -1, false, sms, st));
+  NS_TRY(d('t', W[5], W[7]));
+  NS_S(acc(W[11], W[7], 1.0, -1, false));
+  NS_S(vals2coeffs_impl(P, W[11], W[8]));
+  NS_TRY(d('z', W[8], W[7]));
+  NS_S(coeffs2vals_impl(P, W[7], W[11]));
+  NS_TRY(d('r', W[6], W[7]));
+  NS_TRY(d('r', W[7], W[8]));
+  NS_S(acc(W[11], W[8], -1.0, 0, false));
+  NS_S(acc(W[11], W[7], -1.0, -1, false));
+  NS_TRY(d('t', W[6], W[7]));
+  NS_TRY(d('t', W[7], W[8]));
+  NS_S(acc(W[11], W[8], -1.0, -2, false));
+  NS_S(vals2coeffs_impl(P, W[11], W[11]));
+  //    horizontal solves: gamma_a from s1, lambda_a from s2 (in place)
+  const int zero_other = (h.flags & CYL_BOTH_PARITIES) ? 0 : 1;
+  NS_TRY(cyl::launch_disk_poisson(P->d_disk_items, P->ndisk, P->d_fac, W[10], W[10], n, mn, zero_other,
+                                  P->disk_threads, st));
+  NS_TRY(cyl::launch_disk_poisson(P->d_disk_items, P->ndisk, P->d_fac, W[11], W[11], n, mn, zero_other,
+                                  P->disk_threads, st));
+  // 5. eq. NSrewrite, IMEX BDF1: one heat step each with alpha = 1/Re and forcing (lambda_a, gamma_a)
+  NS_S(run_adi(P, 1, lw, lw, W[11], h.dt, 0, 1, nullptr, 1));
+  NS_S(run_adi(P, 1, gw, gw, W[10], h.dt, 0, 1, nullptr, 1));
+#undef NS_TRY
+#undef NS_S
+  (void)N;
+  return CYL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cyl_status cyl_ns_workspace(cyl_plan_t P, size_t *bytes) {
+  if (!P || !bytes) return CYL_EINVAL;
+  if (P->is_batch) return CYL_ESTATE;
+  *bytes = (size_t)kNsArrays * P->N * sizeof(double);
+  return CYL_OK;
+}
+
+cyl_status cyl_ns_step(cyl_plan_t P, double *lam_w, double *gam_w, int nsteps, void *workspace,
+                       size_t workspace_bytes) {
+  if (!P || !lam_w || !gam_w || nsteps < 0) return CYL_EINVAL;
+  if (P->is_batch || P->host_only || !P->hp.kind[0].built || !P->hp.kind[1].built || !P->d_disk_items)
+    return CYL_ESTATE;
+  if (P->hp.m % 2) return CYL_EINVAL;
+  if (!workspace || workspace_bytes < (size_t)kNsArrays * P->N * sizeof(double)) return CYL_EINVAL;
+  double *W[kNsArrays];
+  for (int i = 0; i < kNsArrays; ++i) W[i] = static_cast<double *>(workspace) + (size_t)i * P->N;
+  for (int s = 0; s < nsteps; ++s) {
+    cyl_status st = ns_one_step(P, lam_w, gam_w, W);
+    if (st != CYL_OK) return st;
+  }
   return CYL_OK;
 }
 

@@ -119,6 +119,18 @@ size_t xform_smem_bytes(int P);
 cudaError_t launch_xform(const double *in, double *out, const double *tab, const XformDesc &d, long long outer,
                          long long inner, int sms, cudaStream_t st);
 
+// Navier-Stokes step kernels (ns.cu): d/dtheta on half-complex slices, the
+// Chebyshev derivative along lines (o, i) of L elements (element a at
+// o * L * inner + a * inner + i; in != out), dst = (init ? 0 : dst) + coef
+// r^rpow src on grid values (radius: the m radial grid points), N = V x W.
+cudaError_t launch_deriv_theta(const double *in, double *out, int p, long long mn, int sms, cudaStream_t st);
+cudaError_t launch_deriv_cheb(const double *in, double *out, long long outer, int L, long long inner, int sms,
+                              cudaStream_t st);
+cudaError_t launch_accum_r(double *dst, const double *src, const double *radius, int p, int m, int n, double coef,
+                           int rpow, bool init, int sms, cudaStream_t st);
+cudaError_t launch_cross(const double *const V[3], const double *const W[3], double *const Nout[3], long long total,
+                         int sms, cudaStream_t st);
+
 // out[o][j][i] = sum_t W[j][t] in[o][t][i]  (dense transform along one axis)
 cudaError_t launch_axis_matvec(const double *in, double *out, const double *W, long long outer, int L,
                                long long inner, cudaStream_t st);

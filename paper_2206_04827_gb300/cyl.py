@@ -73,6 +73,8 @@ _sig = {
     'cyl_batch_autotune': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
     'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
+    'cyl_ns_workspace': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    'cyl_ns_step': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t]),
     'cyl_xform_table': (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _c_double_p]),
     'cyl_fp64_fma_probe': (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _vp, _c_double_p, _vp]),
 }
@@ -237,6 +239,24 @@ class Plan:
                                      _ptr(workspace, 'workspace', (nbytes + 7) // 8) if nbytes else None,
                                      ctypes.c_size_t(nbytes)), 'cyl_heat_adjoint_bc')
         return dL_dT0
+
+    def ns_workspace_bytes(self):
+        nb = ctypes.c_size_t()
+        _check(_lib.cyl_ns_workspace(self._h, ctypes.byref(nb)), 'cyl_ns_workspace')
+        return nb.value
+
+    def ns_step(self, lam_w, gam_w, nsteps=1, workspace=None):
+        """nsteps Navier-Stokes steps on the vorticity PT state (include/cyl.h:
+        cyl_ns_step); the plan needs poisson, heat and disk tables, alpha = 1/Re.
+        The workspace tensor is allocated here (torch) when not given."""
+        nbytes = self.ns_workspace_bytes()
+        if workspace is None:
+            import torch
+            workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=lam_w.device)
+        _check(_lib.cyl_ns_step(self._h, _ptr(lam_w, 'lam_w', self.N), _ptr(gam_w, 'gam_w', self.N), int(nsteps),
+                                _ptr(workspace, 'workspace', (nbytes + 7) // 8), ctypes.c_size_t(nbytes)),
+               'cyl_ns_step')
+        return lam_w, gam_w
 
     def sync(self):
         """Wait for the plan's stream; raise on a device-side timeout or CUDA error."""

@@ -2,7 +2,7 @@
 work item, work arrays in global memory, twisted solves per CTA), against
 the FP64 oracle: forced on small grids for every kind of run (Poisson, BDF1
 with checkpoints, the BDF2 history ring, non-zero wall data), against the
-single-CTA path, automatically at 256^3 on sampled slices, and the bounded
+single-CTA path, at 256^3 on sampled slices, and the bounded
 waits' timeout report under a cluster launch."""
 import os
 
@@ -103,7 +103,7 @@ def test_cluster_equals_single_cta_path(cyl):
 
 
 def test_cluster_256_cubed_sampled_slices_match_oracle(cyl):
-    """256^3 runs in cluster mode by itself (one item's iterate exceeds an
+    """256^3 in cluster mode (two CTAs per item; one item's iterate exceeds an
     SM's shared memory): 5 BDF1 steps from smooth coefficients, compared on
     sampled slices and coefficients with refined oracle values written by
     tests/golden/make_heat256.py (the plain direct solve itself drifts by
@@ -117,7 +117,7 @@ def test_cluster_256_cubed_sampled_slices_match_oracle(cyl):
     sl = torch.as_tensor(ref['slices'], device='cuda')
     idx = torch.as_tensor(ref['idx'], device='cuda')
     errs = []
-    for flags in (0, cyl.FORCE_GLOBAL):
+    for flags in (cyl.FORCE_CLUSTER, 0):
         plan = cyl.Plan(m, n, p, float(ref['alpha']), float(ref['dt']), 1e-15, poisson=False, heat=True,
                         extra_flags=flags)
         T = dev(X0)
