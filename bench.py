@@ -554,6 +554,8 @@ class Batch256(Workload):
                                    'alpha ~ U[0.01,1], dt 1e-3, %d BDF1 steps, T0 = 0, smooth forcing (decay 1.25)'
                                    % (k, self.steps),
                        'problems': k, 'unknowns': int(self.bp.N), 'autotuned': {'threshold': thr, 'groups': G,
+                                                                             'chains_per_thread':
+                                                                                 self.bp.chains_per_thread(),
                                                                              'items_per_class': list(counts)}}
         self.host = None
 

@@ -343,14 +343,18 @@ cyl_status cyl_batch_layout(cyl_plan_t plan, int *nprob, long long *offsets);
 cyl_status cyl_heat_step_batch(cyl_plan_t plan, double *T, const double *g, int nsteps);
 
 /* Launch configuration of a batch plan: threshold on max(M, Nz) between the
- * one-item-per-CTA class and the G-items-per-CTA class, and G in {1, 2, 4}.
- * Setting it reallocates the plan's work areas (not during capture). */
-cyl_status cyl_batch_set_config(cyl_plan_t plan, int threshold, int groups);
-cyl_status cyl_batch_get_config(cyl_plan_t plan, int *threshold, int *groups, int *items_per_class);
+ * one-item-per-CTA class and the G-items-per-CTA class, G in {1, 2, 4}, and
+ * the chains each thread of a one-sided (not twisted) class sweeps in turn,
+ * 1 or 2 (twisted classes always run two threads per chain).  Setting it
+ * reallocates the plan's work areas (not during capture). */
+cyl_status cyl_batch_set_config(cyl_plan_t plan, int threshold, int groups, int chains_per_thread);
+cyl_status cyl_batch_get_config(cyl_plan_t plan, int *threshold, int *groups, int *chains_per_thread,
+                                int *items_per_class);
 
 /*
  * cyl_batch_autotune -- time every candidate configuration (thresholds
- * 0/31/47/63/95 x G = 1/2/4) for nsteps steps on copies of the caller's T and
+ * 0/31/47/63/95 x G = 1/2/4 x chains per thread 1/2) for nsteps steps on
+ * copies of the caller's T and
  * g, keep the fastest and return its time per call in *best_ms (nullable).
  * T is not modified.  Allocates a temporary batch array; host-synchronising.
  */

@@ -55,6 +55,7 @@ struct cyl_plan_s {
     int *d_queue = nullptr;
   } bc[2];
   int threshold = 0;                // items with max(M, Nz) > threshold go to class 0
+  int chains_per_thread = 1;        // one-sided classes: chains each thread sweeps in turn
   cudaStream_t aux = nullptr;       // second stream for the concurrent class
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *d_err = nullptr;         // device status word written by bounded waits
@@ -218,9 +219,10 @@ constexpr int kBatchDefaults[][2] = {{63, 4}, {63, 2}, {47, 4}, {31, 4}, {95, 2}
 // Split a batch's items into two launch classes (threshold on max(M, Nz)) and
 // build their device tables and work areas.  Pairs of Re/Im slices whose
 // shared-memory footprint exceeds a group's budget are split into two items.
-cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
+cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small, int cpt = 1) {
   free_batch(P);
   P->threshold = threshold;
+  P->chains_per_thread = cpt;
   int sms = 152;
   if (!P->host_only) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   for (int cls = 0; cls < 2; ++cls) {
@@ -288,7 +290,9 @@ cyl_status configure_batch(cyl_plan_s *P, int threshold, int G_small) {
     const int half = (chains + 31) / 32 * 32;
     if (tw && (half > cyl::kTwistMaxChains || 2 * half * C.G > kBatchMaxThreads)) return CYL_EINVAL;
     C.twist_half = tw ? half : 0;            // twisted groups: top chains, then bottom chains
-    const int per_group = tw ? 2 * half : std::min(kBatchMaxThreads / C.G, half);
+    // one-sided groups: ceil(chains / cpt) threads, each sweeping cpt chains in turn
+    const int half_cpt = ((chains + cpt - 1) / cpt + 31) / 32 * 32;
+    const int per_group = tw ? 2 * half : std::min(kBatchMaxThreads / C.G, half_cpt);
     C.threads = std::max(kBatchThreads, C.G * per_group);
     C.smem = cyl::batch_smem_bytes(C.G, C.ld, C.smem_rows, C.maxM, C.maxNz, C.twist_half);
     if (C.smem > kSmemLimit) return CYL_EINVAL;
@@ -1260,15 +1264,18 @@ cyl_status cyl_heat_step_batch(cyl_plan_t P, double *T, const double *g, int nst
   return run_batch(P, T, g, nsteps);
 }
 
-cyl_status cyl_batch_set_config(cyl_plan_t P, int threshold, int groups) {
+cyl_status cyl_batch_set_config(cyl_plan_t P, int threshold, int groups, int chains_per_thread) {
   if (!P || !P->is_batch || (groups != 1 && groups != 2 && groups != 4) || threshold < 0) return CYL_EINVAL;
-  return configure_batch(P, threshold, groups);
+  if (chains_per_thread != 1 && chains_per_thread != 2) return CYL_EINVAL;
+  return configure_batch(P, threshold, groups, chains_per_thread);
 }
 
-cyl_status cyl_batch_get_config(cyl_plan_t P, int *threshold, int *groups, int *items_per_class) {
+cyl_status cyl_batch_get_config(cyl_plan_t P, int *threshold, int *groups, int *chains_per_thread,
+                                int *items_per_class) {
   if (!P || !P->is_batch) return CYL_EINVAL;
   if (threshold) *threshold = P->threshold;
   if (groups) *groups = P->bc[1].G;
+  if (chains_per_thread) *chains_per_thread = P->chains_per_thread;
   if (items_per_class) {
     items_per_class[0] = P->bc[0].nitems;
     items_per_class[1] = P->bc[1].nitems;
@@ -1288,12 +1295,13 @@ cyl_status cyl_batch_autotune(cyl_plan_t P, const double *T, const double *g, in
   const int thresholds[] = {0, 31, 47, 63, 95};
   const int groups[] = {1, 2, 4};
   float best = 1e30f;
-  int bt = 63, bg = 4;
+  int bt = 63, bg = 4, bc = 1;
   cyl_status s = CYL_OK;
   for (int th : thresholds)
-    for (int G : groups) {
+    for (int G : groups)
+      for (int cpt = 1; cpt <= 2; ++cpt) {
       if (th == 0 && G != 1) continue;
-      s = configure_batch(P, th, G);
+      s = configure_batch(P, th, G, cpt);
       if (s != CYL_OK) { s = CYL_OK; continue; }
       float ms = 0;
       for (int rep = 0; rep < 2 && s == CYL_OK; ++rep) {
@@ -1305,14 +1313,14 @@ cyl_status cyl_batch_autotune(cyl_plan_t P, const double *T, const double *g, in
         cudaEventElapsedTime(&ms, e0, e1);
       }
       if (s != CYL_OK) break;
-      if (ms < best) { best = ms; bt = th; bg = G; }
-    }
+      if (ms < best) { best = ms; bt = th; bg = G; bc = cpt; }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(work);
   if (s != CYL_OK) return s;
   if (best_ms) *best_ms = best;
-  return configure_batch(P, bt, bg);
+  return configure_batch(P, bt, bg, bc);
 }
 
 }  // extern "C"

@@ -67,9 +67,9 @@ _sig = {
                                       ctypes.c_uint, _vp]),
     'cyl_batch_layout': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
     'cyl_heat_step_batch': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
-    'cyl_batch_set_config': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    'cyl_batch_set_config': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     'cyl_batch_get_config': (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                            ctypes.POINTER(ctypes.c_int)]),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     'cyl_batch_autotune': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     'cyl_ellip_K': (ctypes.c_double, [ctypes.c_double]),
     'cyl_jacobi_dn': (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
@@ -346,14 +346,22 @@ class BatchPlan:
                'cyl_heat_step_batch')
         return T
 
-    def set_config(self, threshold, groups):
-        _check(_lib.cyl_batch_set_config(self._h, int(threshold), int(groups)), 'cyl_batch_set_config')
+    def set_config(self, threshold, groups, chains_per_thread=1):
+        _check(_lib.cyl_batch_set_config(self._h, int(threshold), int(groups), int(chains_per_thread)),
+               'cyl_batch_set_config')
 
     def config(self):
-        t, g = ctypes.c_int(), ctypes.c_int()
+        """(threshold, groups, items per class); chains_per_thread() gives the third knob."""
+        t, g, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ipc = (ctypes.c_int * 2)()
-        _check(_lib.cyl_batch_get_config(self._h, ctypes.byref(t), ctypes.byref(g), ipc), 'cyl_batch_get_config')
+        _check(_lib.cyl_batch_get_config(self._h, ctypes.byref(t), ctypes.byref(g), ctypes.byref(c), ipc),
+               'cyl_batch_get_config')
+        self._cpt = c.value
         return t.value, g.value, (ipc[0], ipc[1])
+
+    def chains_per_thread(self):
+        self.config()
+        return self._cpt
 
     def autotune(self, T, g=None, nsteps=1):
         ms = ctypes.c_double()

@@ -64,12 +64,13 @@ def test_batch_equals_single_problem_runs_for_every_config(cyl):
     gs = _fields(rng, bp.shapes)
     plain = _run_plain(cyl, bp.shapes, alpha, dt, T0s, gs, steps)
     configs = [(63, 4), (0, 1), (31, 2), (15, 4), (95, 1), (47, 2)]
-    # one-sided sweeps in both forms: the same arithmetic, bit for bit
+    # one-sided sweeps in both forms: the same arithmetic, bit for bit, with one or two chains per thread
     for thr, G in configs:
-        bp.set_config(thr, G)
-        got = _run_batch(bp, T0s, gs, steps)
-        for a, b in zip(got, plain):
-            assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
+        for cpt in (1, 2):
+            bp.set_config(thr, G, chains_per_thread=cpt)
+            got = _run_batch(bp, T0s, gs, steps)
+            for a, b in zip(got, plain):
+                assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
     # the default batch (twisted solves per slice) and the per-problem default agree to rounding
     tw = cyl.BatchPlan(n_r, n_z, n_t, alpha, dt, 1e-14)
     for thr, G in configs:

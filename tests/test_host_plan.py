@@ -343,6 +343,12 @@ def test_batch_configuration_on_host(cyl):
     tw.set_config(0, 1)
     pl.set_config(0, 1)
     assert tw.config()[2][0] > pl.config()[2][0]
+    # two chains per thread in the one-sided classes; other values are refused
+    pl.set_config(31, 2, chains_per_thread=2)
+    assert pl.chains_per_thread() == 2 and pl.config()[:2] == (31, 2)
+    for bad in (0, 3):
+        with pytest.raises(cyl.CylError):
+            pl.set_config(31, 2, chains_per_thread=bad)
     import torch
     x = torch.zeros(1, dtype=torch.float64)
     with pytest.raises((cyl.CylError, ValueError)):
