@@ -452,14 +452,17 @@ class Large512(Workload):
     TRAFFIC = (102546660096 + 88557331456 + 1747276132864 + 1472403574784, None)
     TRAFFIC_BASIS = 'ncu capture of the bench step (two launches)'
 
-    def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None, n_theta=L512):
+    def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None, n_theta=L512, cluster=False):
         m = n = L512
         p = n_theta                  # 512 = the workload; fewer only for profiling
         self.torch, self.cyl = torch, cyl
         # ADI tolerance 1e-15: at 1e-14 the 20-step run ends at 1.7e-12 of the (refined) oracle, the
-        # Zolotarev bound being optimistic for the non-normal 512-point pencils
+        # Zolotarev bound being optimistic for the non-normal 512-point pencils.  cluster: the opt-in
+        # cluster mode of the library (a thread-block cluster per item), for comparison.
         self.plan = cyl.Plan(m, n, p, ALPHA_512, DT_512, TOL_512, poisson=True, heat=True,
-                             stream=stream.cuda_stream)
+                             stream=stream.cuda_stream, extra_flags=cyl.FORCE_CLUSTER if cluster else 0)
+        if cluster:
+            self.TRAFFIC = None
         if f_host is None or p != L512:
             f_host = inputs.smooth_coeffs(p, m, n, 1.1, inputs.rng_for(SEED_512))
         if p != L512:
@@ -473,7 +476,8 @@ class Large512(Workload):
         self.kernel = 'adi_kernel'
         self.config = {'workload': '512^3: Poisson solve (f = smooth coefficients, decay 1.1) then 20 BDF1 heat '
                                    'steps (alpha 0.1, dt 1e-4) from its solution; coefficients in / out'
-                                   + ('' if p == L512 else ' [PROFILING CASE: n_theta = %d]' % p),
+                                   + ('' if p == L512 else ' [PROFILING CASE: n_theta = %d]' % p)
+                                   + (' [cluster mode]' if cluster else ''),
                        'n_r': m, 'n_z': n, 'n_theta': p, 'adi_tol': TOL_512,
                        'time_steps_per_bench_step': 1 + self.hsteps,
                        'l2': 'inputs larger than L2 (1.07 GB per field)'}
@@ -768,10 +772,14 @@ class NS128(Workload):
         self.Lw, self.Gw = torch.empty_like(self.L0), torch.empty_like(self.G0)
         self.ws = torch.empty((self.plan.ns_workspace_bytes() + 7) // 8, dtype=torch.float64, device=dev)
         self.units = L ** 3 * self.STEPS
-        # the ADI solves of a step: one Poisson solve and two heat steps
-        self.flops = self.STEPS * (self.plan.flops(0, 1) + 2 * self.plan.flops(1, 1))
+        # FP64 flops of a step: the ADI solves (one Poisson solve, two heat steps) and the 28 chirp-z
+        # transforms (22 coefficient -> value, 6 value -> coefficient; flops as in the xform workloads)
+        info, _ = cyl.xform_table(0, L)
+        per_line = 10 * info['P'] * info['logP'] + 12 * info['P']
+        xflops = 28 * per_line * (2 * L * L + L * L / 2.0)
+        self.flops = self.STEPS * (self.plan.flops(0, 1) + 2 * self.plan.flops(1, 1) + xflops)
         self.launches = self.STEPS * 150
-        self.kernel = 'adi_kernel + chirp_xform_kernel'
+        self.kernel = 'chirp_xform_kernel + adi_kernel'
         self.config = {'workload': 'Navier-Stokes 128^3 (poloidal-toroidal vorticity, IMEX BDF1), Re 100, dt 1e-3, '
                                    '%d steps from smooth seeded potentials' % self.STEPS,
                        'n_r': L, 'n_z': L, 'n_theta': L, 'l2': 'flushed between timed steps (256 MB write)'}
@@ -831,7 +839,8 @@ def run_ours(args):
     from paper_2206_04827_gb300 import cyl
     stream = torch.cuda.current_stream(dev)
     if args.workload == 'large512':
-        wl = Large512(cyl, torch, dev, stream, args.nsteps, f_host=f512, n_theta=args.n_theta)
+        wl = Large512(cyl, torch, dev, stream, args.nsteps, f_host=f512, n_theta=args.n_theta,
+                      cluster=args.cluster)
     else:
         wl = WORKLOADS[args.workload](cyl, torch, dev, stream, args.nsteps)
     f512 = None
@@ -969,6 +978,8 @@ def main():
                     help='problems of the batch256 workload (256 = the workload; fewer only for profiling)')
     ap.add_argument('--n-theta', type=int, default=L512,
                     help='n_theta of the large512 workload (512 = the workload; fewer only for profiling)')
+    ap.add_argument('--cluster', action='store_true',
+                    help='large512 in the opt-in cluster mode of the library (comparison and profiling)')
     ap.add_argument('--nsteps', type=int, default=NSTEPS,
                     help='BDF1 steps per bench step of heat128 (100 = the workload; fewer only for profiling)')
     args = ap.parse_args()

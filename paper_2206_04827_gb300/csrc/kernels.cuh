@@ -113,7 +113,6 @@ constexpr int kMaxXformFfts = 16;     // complex FFTs per CTA
 constexpr int kMaxXformP = 8192;      // largest FFT length (shared memory: 16 P bytes per FFT)
 std::vector<double> xform_tables(int kind, int L, XformDesc &d);
 int xform_ffts_per_cta(int P);
-size_t xform_smem_bytes(int P);
 // Lines along one axis: outer x inner lines of L elements, element a of line
 // (o, i) at o * L * inner + a * inner + i (in may equal out).
 cudaError_t launch_xform(const double *in, double *out, const double *tab, const XformDesc &d, long long outer,

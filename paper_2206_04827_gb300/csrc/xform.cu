@@ -361,43 +361,43 @@ __global__ void __launch_bounds__(256) chirp_xform_kernel(const double *in, doub
 
 }  // namespace
 
+// 32 KB of FFT buffers per CTA (8 FFTs of 256 points): seven 256-thread CTAs per SM, so that the
+// FFT groups of a pass spread over the resident CTAs in nearly whole waves.
 int xform_ffts_per_cta(int P) {
-  int G = (int)(65536 / (16 * (long long)P));
+  int G = (int)(32768 / (16 * (long long)P));
   return G < 1 ? 1 : (G > kMaxXformFfts ? kMaxXformFfts : G);
 }
 
-size_t xform_smem_bytes(int P) { return (size_t)xform_ffts_per_cta(P) * P * 16; }
+
+template <int KIND>
+static cudaError_t launch_xform_t(const double *in, double *out, const double *tab, const XformDesc &d,
+                                  long long outer, long long inner, int G, long long groups, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)G * d.P * 16;
+  cudaError_t e = cudaFuncSetAttribute(chirp_xform_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chirp_xform_kernel<KIND>, 256, smem);
+  if (e != cudaSuccess) return e;
+  // one CTA per FFT group while they fit the resident CTAs, else the resident CTAs loop (grid stride)
+  const long long blocks = std::max(1LL, std::min(groups, (long long)sms * std::max(1, per_sm)));
+  chirp_xform_kernel<KIND><<<(int)blocks, 256, smem, st>>>(in, out, tab, d, outer, inner, G);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_xform(const double *in, double *out, const double *tab, const XformDesc &d, long long outer,
                          long long inner, int sms, cudaStream_t st) {
   const long long nlines = outer * inner;
   if (nlines <= 0) return cudaSuccess;
   const int G = xform_ffts_per_cta(d.P);
-  const size_t smem = (size_t)G * d.P * 16;
   const long long nfft = d.kind <= 1 ? nlines : (nlines + 1) / 2;
-  long long blocks = (nfft + G - 1) / G;
-  const long long cap = (long long)sms * std::max(1, (int)(200 * 1024 / smem)) * 2;
-  if (blocks > cap) blocks = cap;
-  cudaError_t e;
+  const long long groups = (nfft + G - 1) / G;
   switch (d.kind) {
     case 0:
-    case 1:
-      e = cudaFuncSetAttribute(chirp_xform_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      chirp_xform_kernel<0><<<(int)blocks, 256, smem, st>>>(in, out, tab, d, outer, inner, G);
-      break;
-    case 2:
-      e = cudaFuncSetAttribute(chirp_xform_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      chirp_xform_kernel<2><<<(int)blocks, 256, smem, st>>>(in, out, tab, d, outer, inner, G);
-      break;
-    default:
-      e = cudaFuncSetAttribute(chirp_xform_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      chirp_xform_kernel<3><<<(int)blocks, 256, smem, st>>>(in, out, tab, d, outer, inner, G);
-      break;
+    case 1: return launch_xform_t<0>(in, out, tab, d, outer, inner, G, groups, sms, st);
+    case 2: return launch_xform_t<2>(in, out, tab, d, outer, inner, G, groups, sms, st);
+    default: return launch_xform_t<3>(in, out, tab, d, outer, inner, G, groups, sms, st);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace cyl
