@@ -614,7 +614,8 @@ class Adjoint128(Workload):
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
         self.torch = torch
-        self.steps, self.every = 200, 20
+        # 200 steps = the workload; --nsteps below 100 shortens it for profiling (same launches per segment)
+        self.steps, self.every = (200 if nsteps == NSTEPS else nsteps), 20
         self.plan = cyl.Plan(M, N_Z, P, 0.5, DT, TOL, poisson=False, heat=True, stream=stream.cuda_stream)
         r, z, th = self.plan.grid()
         rng = inputs.rng_for(1004)
@@ -640,10 +641,12 @@ class Adjoint128(Workload):
         self.flops = 2 * self.plan.flops(1, self.steps) + self.plan.flops(1, self.steps, transposed=True)
         self.launches = 1 + 2 * (self.steps // self.every) + 1
         self.kernel = 'adi_kernel + adi_adjoint_kernel'
-        self.config = {'workload': 'adjoint 128^3, alpha 0.5, dt 1e-3, 200 BDF1 steps, checkpoint every 20: '
+        self.config = {'workload': 'adjoint 128^3, alpha 0.5, dt 1e-3, %d BDF1 steps, checkpoint every 20: '
                                    'forward run (writing the checkpoints) + gradients of |T_N - T_target|^2 in T0, '
-                                   'space-time g and alpha',
-                       'n_r': M, 'n_z': N_Z, 'n_theta': P, 'units': 'unknowns x 200 steps per gradient evaluation'}
+                                   'space-time g and alpha' % self.steps
+                                   + ('' if self.steps == 200 else ' [PROFILING CASE]'),
+                       'n_r': M, 'n_z': N_Z, 'n_theta': P,
+                       'units': 'unknowns x %d steps per gradient evaluation' % self.steps}
         self.host = None
 
     def step(self):
@@ -981,7 +984,8 @@ def main():
     ap.add_argument('--cluster', action='store_true',
                     help='large512 in the opt-in cluster mode of the library (comparison and profiling)')
     ap.add_argument('--nsteps', type=int, default=NSTEPS,
-                    help='BDF1 steps per bench step of heat128 (100 = the workload; fewer only for profiling)')
+                    help='BDF1 steps per bench step of heat128 (100 = the workload) or adjoint128 (200); '
+                         'other values only for profiling')
     args = ap.parse_args()
     global BATCH_PROBLEMS
     BATCH_PROBLEMS = args.batch_problems
