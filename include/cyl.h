@@ -492,6 +492,18 @@ cyl_status cyl_plan_shifts(cyl_plan_t plan, int which, int k, int parity, int *J
 cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int parity, int *dim,
                              double *out);
 
+/* Launch layout of one kind's ADI kernel (which as above; plans only, not
+ * batch plans: CYL_ESTATE).  info[8] receives {items, threads per CTA,
+ * twisted half (threads per side of a twisted solve, 0: one-sided sweeps),
+ * placement (2: iterate and right side in shared memory, 1: iterate only,
+ * 0: both in the per-item global work area), dynamic shared memory bytes,
+ * CTAs per item (1, or the cluster size in cluster mode), slices per item
+ * (the largest), built (0 when the kind was not built)}.  Items whose two
+ * slices leave shared memory are split into single-slice items with twisted
+ * solves on two threads per chain (up to 2 x 256 threads), unless
+ * CYL_PLAIN_SWEEPS or cluster mode is given. */
+cyl_status cyl_plan_launch_info(cyl_plan_t plan, int which, int *info);
+
 /* Host copy of one work item's factor records for ADI iteration j (the
  * tables the kernels read; layout in the library's plan header: radial
  * records of 12 doubles per class row, vertical records of 8 per class

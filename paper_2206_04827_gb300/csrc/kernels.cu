@@ -1398,9 +1398,12 @@ static cudaError_t launch_adjoint_t(const AdiArgs &a, const AdjointArgs &g, int 
 template <bool S_SMEM, bool F_SMEM>
 static cudaError_t launch_adjoint_level(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem,
                                         cudaStream_t st) {
-  if (a.twist_half > 0)     // twisted records: at most 2 x 128 threads
-    return threads <= 128 ? launch_adjoint_t<S_SMEM, F_SMEM, 128, true>(a, g, threads, smem, st)
-                          : launch_adjoint_t<S_SMEM, F_SMEM, 256, true>(a, g, threads, smem, st);
+  if (a.twist_half > 0) {   // twisted records: 2 x 128 threads, or 2 x 256 with Fa in global memory
+    if (threads <= 128) return launch_adjoint_t<S_SMEM, F_SMEM, 128, true>(a, g, threads, smem, st);
+    if (threads <= 256) return launch_adjoint_t<S_SMEM, F_SMEM, 256, true>(a, g, threads, smem, st);
+    if constexpr (!F_SMEM) return launch_adjoint_t<S_SMEM, false, 512, true>(a, g, threads, smem, st);
+    else return cudaErrorInvalidValue;
+  }
   return threads <= 256 ? launch_adjoint_t<S_SMEM, F_SMEM, 256, false>(a, g, threads, smem, st)
                         : launch_adjoint_t<S_SMEM, F_SMEM, 512, false>(a, g, threads, smem, st);
 }
@@ -1409,7 +1412,7 @@ static cudaError_t launch_adjoint_level(const AdiArgs &a, const AdjointArgs &g, 
 // most 256 threads get the full register budget.
 cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || g.n_hi <= g.n_lo) return cudaSuccess;
-  if (a.twist_half > 0 && threads > 256) return cudaErrorInvalidValue;
+  if (threads > 512) return cudaErrorInvalidValue;
   if (a.use_smem == 2) return launch_adjoint_level<true, true>(a, g, threads, smem, st);
   if (a.use_smem == 1) return launch_adjoint_level<true, false>(a, g, threads, smem, st);
   return launch_adjoint_level<false, false>(a, g, threads, smem, st);
@@ -1426,9 +1429,12 @@ static cudaError_t launch_adi_t(const AdiArgs &a, int threads, size_t smem, cuda
 
 template <bool S_SMEM, bool F_SMEM>
 static cudaError_t launch_adi_level(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
-  if (a.twist_half > 0)     // twisted plans use at most 2 x 128 threads
-    return threads <= 128 ? launch_adi_t<S_SMEM, F_SMEM, 128, true>(a, threads, smem, st)
-                          : launch_adi_t<S_SMEM, F_SMEM, 256, true>(a, threads, smem, st);
+  if (a.twist_half > 0) {   // twisted plans: 2 x 128 threads, or 2 x 256 with Fa in global memory
+    if (threads <= 128) return launch_adi_t<S_SMEM, F_SMEM, 128, true>(a, threads, smem, st);
+    if (threads <= 256) return launch_adi_t<S_SMEM, F_SMEM, 256, true>(a, threads, smem, st);
+    if constexpr (!F_SMEM) return launch_adi_t<S_SMEM, false, 512, true>(a, threads, smem, st);
+    else return cudaErrorInvalidValue;
+  }
   return threads <= 128   ? launch_adi_t<S_SMEM, F_SMEM, 128, false>(a, threads, smem, st)
          : threads <= 256 ? launch_adi_t<S_SMEM, F_SMEM, 256, false>(a, threads, smem, st)
                           : launch_adi_t<S_SMEM, F_SMEM, 512, false>(a, threads, smem, st);
@@ -1439,7 +1445,7 @@ static cudaError_t launch_adi_level(const AdiArgs &a, int threads, size_t smem, 
 cudaError_t launch_adi(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
   if (a.nitems <= 0 || a.nsteps <= 0) return cudaSuccess;
   if (a.cluster > 1) return launch_adi_cluster(a, threads, smem, st);
-  if (a.twist_half > 0 && threads > 256) return cudaErrorInvalidValue;
+  if (threads > 512) return cudaErrorInvalidValue;
   if (a.use_smem == 2) return launch_adi_level<true, true>(a, threads, smem, st);
   if (a.use_smem == 1) return launch_adi_level<true, false>(a, threads, smem, st);
   return launch_adi_level<false, false>(a, threads, smem, st);

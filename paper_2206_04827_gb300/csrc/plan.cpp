@@ -607,9 +607,11 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
   // twisted solves only where both sweeps' chains (two slices x class size) fit kTwistMaxChains:
   // there the second half of the threads doubles the warps per SM sub-partition
   const int maxclass = std::max(std::max(hp.Mc[0], hp.Mc[1]), std::max(hp.Nc[0], hp.Nc[1]));
-  // twist == 3 (cluster plans): every item, each CTA of its cluster owning at most kTwistMaxChains chains
+  // twist == 3 (cluster plans): every item, each CTA of its cluster owning at most kTwistMaxChains chains;
+  // twist == 4 (work arrays in global memory): every item, one slice per item
+  if (twist == 4 && maxclass > kTwistMaxChainsGlobal) return "twisted single-slice items need class sizes <= 256";
   const bool tw_ok = (twist == 1 && 2 * maxclass <= kTwistMaxChains) || (twist == 2 && maxclass <= kTwistMaxChains) ||
-                     twist == 3;
+                     twist == 3 || twist == 4;
   for (int kind = 0; kind < kNumKinds; ++kind) {
     KindTables &KT = hp.kind[kind];
     KT = KindTables();
@@ -675,6 +677,7 @@ std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, dou
           };
           if (k == 0) add_item(0, 1);
           else if (k == h) add_item(p - 1, 1);
+          else if (twist == 4) { add_item(2 * k - 1, 1); add_item(2 * k, 1); }
           else add_item(2 * k - 1, 2);
         }
       }

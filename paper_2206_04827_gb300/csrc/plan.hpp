@@ -63,6 +63,9 @@ constexpr int RTWIST = 24;
 constexpr int ZTWIST = 16;
 constexpr int kTwistMinM = 10, kTwistMinN = 8;
 constexpr int kTwistMaxChains = 128;
+// twisted sweeps with the work arrays in global memory (twist mode 4): one
+// CTA of 2 x 256 threads per single-slice item
+constexpr int kTwistMaxChainsGlobal = 256;
 // Horizontal (disk) Poisson: LU records of -L_k (recombined, tau rows) per
 // class row: [0..1] -L[i][i-1], -L[i][i-2]; [2..4] -U[i][i+1..i+3]/U[i][i];
 // [5] 1/U[i][i].
@@ -140,7 +143,9 @@ struct HostPlan {
 // sweeps of a two-slice item have at most kTwistMaxChains chains; 2 = where
 // one slice has (batch plans, which split twisted pairs into single slices);
 // 3 = every item (cluster plans: each CTA of an item's cluster owns at most
-// kTwistMaxChains chains of every sweep).
+// kTwistMaxChains chains of every sweep); 4 = every item, with single-slice
+// items (grids whose work arrays leave shared memory: one CTA of two threads
+// per chain, at most kTwistMaxChainsGlobal chains per sweep).
 std::string build_host_plan(HostPlan &hp, int m, int n, int p, double alpha, double dt, double tol,
                             unsigned flags, int bdf_order = 1, int twist = 1);
 

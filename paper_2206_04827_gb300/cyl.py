@@ -38,6 +38,7 @@ _sig = {
                                             ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t]),
     'cyl_heat_adjoint_bdf_workspace': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       ctypes.POINTER(ctypes.c_size_t)]),
+    'cyl_plan_launch_info': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     'cyl_plan_item_tables': (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int), _c_double_p, _c_double_p]),
     'cyl_disk_poisson': (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -284,6 +285,13 @@ class Plan:
         qs = (ctypes.c_double * J.value)()
         _check(_lib.cyl_plan_shifts(self._h, which, k, parity, ctypes.byref(J), iv, ps, qs), 'cyl_plan_shifts')
         return J.value, tuple(iv), np.array(ps), np.array(qs)
+
+    def launch_info(self, which):
+        """Launch layout of one kind's ADI kernel (see include/cyl.h: cyl_plan_launch_info)."""
+        info = (ctypes.c_int * 8)()
+        _check(_lib.cyl_plan_launch_info(self._h, which, info), 'cyl_plan_launch_info')
+        keys = ('items', 'threads', 'twist_half', 'placement', 'smem', 'ctas_per_item', 'slices', 'built')
+        return dict(zip(keys, list(info)))
 
     def item_tables(self, which, item, j, transposed=False):
         """(info dict, radial records, vertical records) of one item's ADI iteration j

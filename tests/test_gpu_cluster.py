@@ -107,8 +107,10 @@ def test_cluster_256_cubed_sampled_slices_match_oracle(cyl):
     SM's shared memory): 5 BDF1 steps from smooth coefficients, compared on
     sampled slices and coefficients with refined oracle values written by
     tests/golden/make_heat256.py (the plain direct solve itself drifts by
-    ~3e-12 over these steps on the k = 0 slice); the single-CTA global-memory
-    path (one-sided sweeps) is held to the same values."""
+    ~3e-12 over these steps on the k = 0 slice); the default launch
+    (single-slice items, twisted solves, iterate in shared memory) and the
+    plain one (two-slice items, one-sided sweeps, global work arrays) are held
+    to the same values."""
     ref = np.load(GOLD256)
     p = m = n = 256
     rng = inputs.rng_for(int(ref['seed']))
@@ -117,16 +119,19 @@ def test_cluster_256_cubed_sampled_slices_match_oracle(cyl):
     sl = torch.as_tensor(ref['slices'], device='cuda')
     idx = torch.as_tensor(ref['idx'], device='cuda')
     errs = []
-    for flags in (cyl.FORCE_CLUSTER, 0):
+    for flags in (cyl.FORCE_CLUSTER, 0, cyl.PLAIN_SWEEPS):
         plan = cyl.Plan(m, n, p, float(ref['alpha']), float(ref['dt']), 1e-15, poisson=False, heat=True,
                         extra_flags=flags)
+        if flags == 0:
+            li = plan.launch_info(1)
+            assert (li['slices'], li['twist_half'], li['placement']) == (1, 128, 1), li
         T = dev(X0)
         plan.heat_step(T, dev(g), int(ref['steps']))
         plan.sync()
         got = T.index_select(0, sl).index_select(1, idx).index_select(2, idx).cpu().numpy()
         errs.append(relerr(got, ref['heat']))
         plan.close()
-    print('256^3 vs refined oracle: cluster %.2e, single-CTA global %.2e' % tuple(errs))
+    print('256^3 vs refined oracle: cluster %.2e, default %.2e, plain %.2e' % tuple(errs))
     assert max(errs) <= TOL_SOLVE, errs
 
 

@@ -314,6 +314,32 @@ def test_cluster_plans_twist_every_item(cyl):
     plan.close()
 
 
+@pytest.mark.parametrize('mnp,flags,want', [
+    ((512, 512, 512), 0, (1, 256, 512, 0)),          # two-slice arrays leave shared memory: twisted single slices
+    ((512, 512, 512), 'plain', (2, 0, 512, 0)),
+    ((300, 300, 4), 0, (1, 160, 320, 0)),
+    ((256, 256, 256), 0, (1, 128, 256, 1)),          # a single slice's iterate fits shared memory
+    ((128, 128, 128), 0, (2, 128, 256, 2)),          # two-slice items in shared memory, twisted
+    ((128, 128, 128), 'plain', (2, 0, 128, 2)),
+    ((20, 19, 8), 'global', (1, 32, 64, 0)),
+    ((8, 520, 4), 0, (2, 0, 512, 1)),                # 518 radial chains on 512 threads
+    ((600, 600, 8), 0, (2, 0, 512, 0)),              # class sizes above 256: one-sided, threads loop
+])
+def test_launch_layouts(cyl, mnp, flags, want):
+    """(slices per item, twisted half, threads, placement) of the heat
+    kernel's launch as the plan chooses it."""
+    extra = {0: 0, 'plain': cyl.PLAIN_SWEEPS, 'global': cyl.FORCE_GLOBAL}[flags]
+    plan = cyl.Plan(*mnp, 0.1, 1e-4, 1e-14, poisson=True, heat=True, host_only=True, extra_flags=extra)
+    li = plan.launch_info(1)
+    assert (li['slices'], li['twist_half'], li['threads'], li['placement']) == want, li
+    assert li['built'] == 1 and li['ctas_per_item'] == 1 and li['smem'] <= 226 * 1024
+    m, n, p = mnp
+    h = p // 2
+    pairs = h - 1
+    assert li['items'] == 2 * ((2 * pairs if want[0] == 1 else pairs) + 2)   # x 2 vertical parity classes
+    plan.close()
+
+
 def test_batch_configuration_on_host(cyl):
     """Host-only batch plan of uneven grids: a feasible default (threshold,
     groups) is chosen at plan time, every accepted setting assigns all
