@@ -118,6 +118,21 @@ def _oracle_worker_512(args):
     return time.perf_counter() - t0, {s: T[s].copy()}
 
 
+def _adi_worker_512(args):
+    """The same slice through the CPU ADI of the oracle package (Algorithm 1
+    with the paper's shifts, banded solves): the second CPU baseline, the
+    GPU's own algorithm on the host cores."""
+    sys.path.insert(0, ROOT)
+    from oracle import adi as oadi
+    s, fs, steps = args
+    F = np.zeros((L512, L512, L512))
+    F[s] = fs
+    t0 = time.perf_counter()
+    u = oadi.poisson(F, TOL_512, slices=[s])
+    T = oadi.heat_steps(u, F, ALPHA_512, DT_512, steps, TOL_512, slices=[s])
+    return time.perf_counter() - t0, {s: T[s].copy()}
+
+
 class OracleSampler:
     """The oracle as it stands, timed on the host cores over a bounded sample
     of a workload: one sampled theta-slice per task, tasks spread over
@@ -125,7 +140,7 @@ class OracleSampler:
     sampled unknowns*steps / (summed solve time / workers); process start-up,
     imports and input generation excluded."""
 
-    def __init__(self, workload, nslices, steps, procs=None, f512=None):
+    def __init__(self, workload, nslices, steps, procs=None, f512=None, algo='direct'):
         self.workload, self.steps = workload, steps
         self.procs = min(procs or os.cpu_count() or 1, nslices)
         if workload == 'large512':
@@ -134,11 +149,14 @@ class OracleSampler:
             if f512 is None:
                 f512 = inputs.smooth_coeffs(L512, L512, L512, 1.1, inputs.rng_for(SEED_512))
             self.jobs = [(s, np.ascontiguousarray(f512[s]), steps) for s in self.slices]
-            self.fn = _oracle_worker_512
+            self.fn = _oracle_worker_512 if algo == 'direct' else _adi_worker_512
             self.units = nslices * L512 * L512 * (1 + steps)
+            how = ('QZ Bartels-Stewart per slice, including its per-wavenumber QZ set-up' if algo == 'direct' else
+                   'ADI of Algorithm 1 with the Zolotarev shifts, scipy banded solves, tolerance %g, including the '
+                   'per-wavenumber eigenvalue and shift set-up' % TOL_512)
             self.sample = ('%d of %d theta-slices of the 512^3 workload, each: Poisson solve + %d BDF1 heat steps '
-                           '(QZ Bartels-Stewart per slice, including its per-wavenumber QZ set-up), spread over %d '
-                           'single-threaded worker processes (solve time only)' % (nslices, L512, steps, self.procs))
+                           '(%s), spread over %d single-threaded worker processes (solve time only)'
+                           % (nslices, L512, steps, how, self.procs))
         else:
             self.L = P
             self.slices = [int(x) for x in np.linspace(0, P - 1, nslices).round()]
@@ -832,12 +850,17 @@ def run_ours(args):
 
     # CPU baseline first (the pool is spawned; the sample runs before heavy GPU use)
     cpu, cpu_res, f512 = None, None, None
+    cpu_adi, cpu_adi_res = None, None
     if args.workload == 'large512' and args.n_theta == L512:
         f512 = inputs.smooth_coeffs(L512, L512, L512, 1.1, inputs.rng_for(SEED_512))
     if rank == 0 and not args.no_cpu_baseline and args.workload in CPU_LEGS and args.n_theta == L512:
         cpu = OracleSampler(args.workload, args.cpu_slices, args.cpu_steps, f512=f512)
         cpu_res = cpu.run()
         cpu.close()
+        if args.workload == 'large512' and not args.no_cpu_adi:
+            cpu_adi = OracleSampler(args.workload, args.cpu_slices, args.cpu_steps, f512=f512, algo='adi')
+            cpu_adi_res = cpu_adi.run()
+            cpu_adi.close()
 
     from paper_2206_04827_gb300 import cyl
     stream = torch.cuda.current_stream(dev)
@@ -924,6 +947,9 @@ def run_ours(args):
     if cpu is not None:
         line['cpu_baseline'] = {'value': cpu_res[0], 'unit': UNIT, 'cores': cpu.procs, 'kind': 'oracle',
                                 'sample': cpu.sample}
+    if cpu_adi is not None:
+        line['cpu_baseline_adi'] = {'value': cpu_adi_res[0], 'unit': UNIT, 'cores': cpu_adi.procs,
+                                    'kind': 'same algorithm on the CPU (numpy/scipy)', 'sample': cpu_adi.sample}
     line.update(acc)
     line.update(wl.extra(stream, 20))
     if isinstance(wl, Batch256):
@@ -977,6 +1003,8 @@ def main():
     ap.add_argument('--cpu-steps', type=int, default=None,
                     help='heat steps per sampled slice (default: 2 after the Poisson solve at 512^3, 30 at 128^3)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-cpu-adi', action='store_true',
+                    help='skip the second CPU baseline of the 512^3 workload (the CPU ADI)')
     ap.add_argument('--batch-problems', type=int, default=256,
                     help='problems of the batch256 workload (256 = the workload; fewer only for profiling)')
     ap.add_argument('--n-theta', type=int, default=L512,
