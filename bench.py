@@ -63,15 +63,20 @@ FP64_FMA_PER_CLK_PER_SM = 2      # the FP64 pipe's issue rate, confirmed live by
 GOLD512 = os.path.join(ROOT, 'tests', 'golden', 'large512_sampled.npz')
 
 
-def source_hash():
-    """Short hash of the CUDA/C++ sources of libcyl: DRAM-traffic figures taken
-    from an ncu capture are valid only for the kernel source they were taken
-    on, and are reported as stale once it changes."""
+# sources that decide the ADI kernels' code, tables and launch layout
+ADI_SOURCES = ('api.cu', 'kernels.cu', 'kernels.cuh', 'plan.cpp', 'plan.hpp')
+
+
+def source_hash(files=None):
+    """Short hash of the CUDA/C++ sources of libcyl (all of them, or the named
+    files of csrc/) and of include/cyl.h: DRAM-traffic figures taken from an
+    ncu capture are valid only for the kernel source they were taken on, and
+    are reported as stale once it changes."""
     import hashlib
     d = os.path.join(ROOT, 'paper_2206_04827_gb300', 'csrc')
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith(('.cu', '.cuh', '.cpp', '.hpp')):
+        if f.endswith(('.cu', '.cuh', '.cpp', '.hpp')) and (files is None or f in files):
             with open(os.path.join(d, f), 'rb') as fh:
                 h.update(f.encode() + b'\0' + fh.read())
     with open(os.path.join(ROOT, 'include', 'cyl.h'), 'rb') as fh:
@@ -256,8 +261,9 @@ def traffic_of(wl):
     if wl.TRAFFIC is None:
         return None, 'no ncu capture for this workload'
     nbytes, src = wl.TRAFFIC
-    if src != source_hash():
-        return None, 'stale: kernel source changed since the ncu capture (source %s, now %s)' % (src, source_hash())
+    now = source_hash(wl.TRAFFIC_SOURCES)
+    if src != now:
+        return None, 'stale: kernel source changed since the ncu capture (source %s, now %s)' % (src, now)
     return wl.traffic_scale(nbytes), wl.TRAFFIC_BASIS + ' (kernel source %s)' % src
 
 
@@ -320,6 +326,7 @@ class Workload:
     config = {}
     TRAFFIC = None
     TRAFFIC_BASIS = ''
+    TRAFFIC_SOURCES = ADI_SOURCES    # the files whose hash TRAFFIC was taken at
     cpu = None                  # OracleSampler of this workload's CPU baseline, when it has one
 
     def traffic_scale(self, nbytes):
@@ -464,11 +471,15 @@ class Poisson33(Workload):
 
 class Large512(Workload):
     name = 'large512'
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches (Poisson
-    # 102,546,660,096 + 88,557,331,456; 20 heat steps 1,747,276,132,864 + 1,472,403,574,784), taken
-    # before the kernel-source hash was recorded: reported as stale until captured again
-    TRAFFIC = (102546660096 + 88557331456 + 1747276132864 + 1472403574784, None)
-    TRAFFIC_BASIS = 'ncu capture of the bench step (two launches)'
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches on the same
+    # workload with n_theta = 320 (Poisson 36,376,811,520 + 41,409,028,608; 20 heat steps
+    # 616,543,005,952 + 647,541,979,648), scaled to n_theta = 512 by the items processed
+    TRAFFIC = (36376811520 + 41409028608 + 616543005952 + 647541979648, '722528673eaf')
+    TRAFFIC_BASIS = 'ncu capture of the step at n_theta = 320 (two launches), scaled by 512 / 320'
+    TRAFFIC_NTHETA = 320
+
+    def traffic_scale(self, nbytes):
+        return nbytes * self.f.shape[0] / self.TRAFFIC_NTHETA
 
     def __init__(self, cyl, torch, dev, stream, nsteps, f_host=None, n_theta=L512, cluster=False):
         m = n = L512
@@ -943,6 +954,7 @@ def run_ours(args):
         'clocks': {k: clocks[k] for k in ('sm_mhz', 'sm_max_mhz', 'reasons')},
         'wall_s': wall,
         'kernel_source': source_hash(),
+        'adi_source': source_hash(ADI_SOURCES),
     }
     if cpu is not None:
         line['cpu_baseline'] = {'value': cpu_res[0], 'unit': UNIT, 'cores': cpu.procs, 'kind': 'oracle',
