@@ -198,45 +198,131 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// One pass over G complex FFT buffers of length P (radix-2).  DIF forward:
-// natural -> bit-reversed.  DIT inverse with conjugate twiddles:
-// bit-reversed -> natural.
+// G complex FFT buffers of length P in shared memory, radix-2 stages fused
+// in pairs: each thread takes a quad of elements through two stages in
+// registers (half the shared-memory passes and barriers of one stage at a
+// time, the same operations in the same order).  The two stages of span 1
+// and 2 need no multiplication: their twiddles are tw[0] = 1 and
+// tw[P/4] = -i, which the host tables hold exactly, so (a, b) * -i is
+// (b, -a) and the results equal those of the full complex products.
+// DIF forward: natural -> bit-reversed.  DIT inverse with conjugate
+// twiddles: bit-reversed -> natural.
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// one DIF stage of span h = 2^lh over all G buffers
+__device__ __forceinline__ void dif_stage(double2 *buf, int G, int P, int lh, const double2 *__restrict__ tw) {
+  const int half = P >> 1, h = 1 << lh, tstep = half >> lh;
+  for (int b = threadIdx.x; b < G * half; b += blockDim.x) {
+    const int g = b / half, r = b - g * half;
+    const int pos = r & (h - 1), grp = r >> lh;
+    double2 *x = buf + (size_t)g * P + grp * 2 * h + pos;
+    const double2 x0 = x[0], x1 = x[h];
+    x[0] = cadd(x0, x1);
+    x[h] = cmul(csub(x0, x1), __ldg(tw + pos * tstep));
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void fft_dif(double2 *buf, int G, int P, int logP, const double2 *__restrict__ tw) {
-  const int half = P >> 1;
-  for (int lh = logP - 1; lh >= 0; --lh) {
-    const int h = 1 << lh;
-    const int tstep = half >> lh;          // P / (2h)
-    for (int b = threadIdx.x; b < G * half; b += blockDim.x) {
-      const int g = b / half, r = b - g * half;
-      const int pos = r & (h - 1), grp = r >> lh;
-      double2 *x = buf + (size_t)g * P + grp * 2 * h + pos;
-      const double2 x0 = x[0], x1 = x[h];
-      const double2 w = __ldg(tw + pos * tstep);
-      x[0] = make_double2(x0.x + x1.x, x0.y + x1.y);
-      x[h] = cmul(make_double2(x0.x - x1.x, x0.y - x1.y), w);
+  const int quarter = P >> 2;
+  int lh = logP - 1;
+  // stage pairs (lh, lh - 1), spans H and H/2, on quads pos, pos + H/2, pos + H, pos + 3H/2 of a 2H block
+  for (; lh >= 3; lh -= 2) {
+    const int H2 = 1 << (lh - 1), ts1 = (P >> 1) >> lh, ts2 = 2 * ts1;
+    for (int b = threadIdx.x; b < G * quarter; b += blockDim.x) {
+      const int g = b / quarter, q = b - g * quarter;
+      const int pos = q & (H2 - 1), blk = q >> (lh - 1);
+      double2 *x = buf + (size_t)g * P + blk * 4 * H2 + pos;
+      const double2 a0 = x[0], a1 = x[H2], a2 = x[2 * H2], a3 = x[3 * H2];
+      const double2 w1 = __ldg(tw + pos * ts1), w1b = __ldg(tw + (pos + H2) * ts1), w2 = __ldg(tw + pos * ts2);
+      const double2 b0 = cadd(a0, a2), b2 = cmul(csub(a0, a2), w1);
+      const double2 b1 = cadd(a1, a3), b3 = cmul(csub(a1, a3), w1b);
+      x[0] = cadd(b0, b1);
+      x[H2] = cmul(csub(b0, b1), w2);
+      x[2 * H2] = cadd(b2, b3);
+      x[3 * H2] = cmul(csub(b2, b3), w2);
     }
     __syncthreads();
+  }
+  if (lh == 2) {
+    dif_stage(buf, G, P, 2, tw);
+    lh = 1;
+  }
+  if (lh == 1) {      // spans 2 and 1 on quads of consecutive elements: twiddles 1 and -i, then 1
+    for (int b = threadIdx.x; b < G * quarter; b += blockDim.x) {
+      double2 *x = buf + (size_t)4 * b;
+      const double2 a0 = x[0], a1 = x[1], a2 = x[2], a3 = x[3];
+      const double2 b0 = cadd(a0, a2), b2 = csub(a0, a2);
+      const double2 b1 = cadd(a1, a3), d13 = csub(a1, a3);
+      const double2 b3 = make_double2(d13.y, -d13.x);
+      x[0] = cadd(b0, b1);
+      x[1] = csub(b0, b1);
+      x[2] = cadd(b2, b3);
+      x[3] = csub(b2, b3);
+    }
+    __syncthreads();
+  } else if (lh == 0) {
+    dif_stage(buf, G, P, 0, tw);
   }
 }
 
+// one DIT stage (conjugate twiddles) of span h = 2^lh
+__device__ __forceinline__ void dit_stage(double2 *buf, int G, int P, int lh, const double2 *__restrict__ tw) {
+  const int half = P >> 1, h = 1 << lh, tstep = half >> lh;
+  for (int b = threadIdx.x; b < G * half; b += blockDim.x) {
+    const int g = b / half, r = b - g * half;
+    const int pos = r & (h - 1), grp = r >> lh;
+    double2 *x = buf + (size_t)g * P + grp * 2 * h + pos;
+    const double2 x0 = x[0];
+    const double2 t = cmul(x[h], cconj(__ldg(tw + pos * tstep)));
+    x[0] = cadd(x0, t);
+    x[h] = csub(x0, t);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void fft_dit_inv(double2 *buf, int G, int P, int logP, const double2 *__restrict__ tw) {
-  const int half = P >> 1;
-  for (int lh = 0; lh < logP; ++lh) {
-    const int h = 1 << lh;
-    const int tstep = half >> lh;
-    for (int b = threadIdx.x; b < G * half; b += blockDim.x) {
-      const int g = b / half, r = b - g * half;
-      const int pos = r & (h - 1), grp = r >> lh;
-      double2 *x = buf + (size_t)g * P + grp * 2 * h + pos;
-      const double2 x0 = x[0];
-      double2 w = __ldg(tw + pos * tstep);
-      w.y = -w.y;
-      const double2 t = cmul(x[h], w);
-      x[0] = make_double2(x0.x + t.x, x0.y + t.y);
-      x[h] = make_double2(x0.x - t.x, x0.y - t.y);
+  const int quarter = P >> 2;
+  int lh = 0;
+  if (logP >= 2) {    // spans 1 and 2 on quads of consecutive elements: twiddles 1, then 1 and +i
+    for (int b = threadIdx.x; b < G * quarter; b += blockDim.x) {
+      double2 *x = buf + (size_t)4 * b;
+      const double2 a0 = x[0], a1 = x[1], a2 = x[2], a3 = x[3];
+      const double2 b0 = cadd(a0, a1), b1 = csub(a0, a1);
+      const double2 b2 = cadd(a2, a3), b3 = csub(a2, a3);
+      const double2 t3 = make_double2(-b3.y, b3.x);
+      x[0] = cadd(b0, b2);
+      x[2] = csub(b0, b2);
+      x[1] = cadd(b1, t3);
+      x[3] = csub(b1, t3);
+    }
+    __syncthreads();
+    lh = 2;
+  }
+  // stage pairs (lh, lh + 1), spans h and 2h, on quads pos, pos + h, pos + 2h, pos + 3h of a 4h block
+  for (; lh + 1 < logP; lh += 2) {
+    const int h = 1 << lh, tsA = (P >> 1) >> lh, tsB = tsA >> 1;
+    for (int b = threadIdx.x; b < G * quarter; b += blockDim.x) {
+      const int g = b / quarter, q = b - g * quarter;
+      const int pos = q & (h - 1), blk = q >> lh;
+      double2 *x = buf + (size_t)g * P + blk * 4 * h + pos;
+      const double2 a0 = x[0], a1 = x[h], a2 = x[2 * h], a3 = x[3 * h];
+      const double2 wA = cconj(__ldg(tw + pos * tsA));
+      const double2 wB = cconj(__ldg(tw + pos * tsB)), wBb = cconj(__ldg(tw + (pos + h) * tsB));
+      const double2 t1 = cmul(a1, wA), t3 = cmul(a3, wA);
+      const double2 b0 = cadd(a0, t1), b1 = csub(a0, t1);
+      const double2 b2 = cadd(a2, t3), b3 = csub(a2, t3);
+      const double2 u2 = cmul(b2, wB), u3 = cmul(b3, wBb);
+      x[0] = cadd(b0, u2);
+      x[2 * h] = csub(b0, u2);
+      x[h] = cadd(b1, u3);
+      x[3 * h] = csub(b1, u3);
     }
     __syncthreads();
   }
+  if (lh < logP) dit_stage(buf, G, P, lh, tw);
 }
 
 // KIND 0: DCT-I (forward or inverse by its tables), one real line per FFT.
@@ -246,7 +332,7 @@ __device__ __forceinline__ void fft_dit_inv(double2 *buf, int G, int P, int logP
 // at o * L * inner + a * inner + i.  in may equal out (each CTA reads all
 // its lines before it writes them).
 template <int KIND>
-__global__ void __launch_bounds__(256) chirp_xform_kernel(const double *in, double *out, const double *tab,
+__global__ void __launch_bounds__(256, 6) chirp_xform_kernel(const double *in, double *out, const double *tab,
                                                           XformDesc d, long long outer, long long inner, int G) {
   extern __shared__ __align__(16) double2 xbuf[];
   const double2 *pre = reinterpret_cast<const double2 *>(tab + d.pre_off);
