@@ -347,9 +347,8 @@ class Workload:
 
 class Heat128(Workload):
     name = 'heat128'
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch, taken before
-    # the kernel-source hash was recorded: reported as stale until captured again
-    TRAFFIC = (49261312 + 1183488, None)
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch of the bench
+    TRAFFIC = (49169920 + 1013504, '722528673eaf')
     TRAFFIC_BASIS = 'ncu capture of the bench launch'
 
     def __init__(self, cyl, torch, dev, stream, nsteps):

@@ -31,9 +31,10 @@
 // conjugate twiddles for the inverse (bit-reversed in, natural out): no
 // permutation pass.  G complex FFTs of one CTA live in shared memory.
 //
-// FP64 work per complex FFT: 8 operations per butterfly, P/2 log2 P
-// butterflies; the transforms are bound by the FP64 pipe (GB300's FP64 rate
-// is far below its memory bandwidth), not by HBM.
+// FP64 work per complex FFT: P/2 log2 P butterflies of 8 operations (4 in
+// the two stages whose twiddles are 1 and -i); the transforms are bound by
+// the FP64 pipe (GB300's FP64 rate is far below its memory bandwidth), not by
+// HBM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
