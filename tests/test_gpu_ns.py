@@ -50,6 +50,26 @@ def test_ns_steps_match_oracle(cyl, m, n, p, steps):
     assert relerr(G.cpu().numpy(), want_g) <= TOL_SOLVE
 
 
+def test_ns_128_bench_state_matches_oracle(cyl):
+    """The Navier-Stokes workload at full size, in the bench's launch
+    configuration (128^3, Re 100, dt 1e-3, ADI tolerance 1e-14, the bench's
+    seeded potentials): one step compared with the oracle's step on every
+    coefficient (the nonlinear term couples all slices, so the oracle computes
+    the whole field; about a minute on the host)."""
+    L = 128
+    rng = inputs.rng_for(1005)
+    Lw = inputs.smooth_coeffs(L, L, L, 1.25, rng)
+    Gw = inputs.smooth_coeffs(L, L, L, 1.25, rng)
+    plan = cyl.Plan(L, L, L, 1.0 / 100.0, 1e-3, 1e-14, poisson=True, heat=True, extra_flags=cyl.WITH_DISK)
+    l, g = dev(Lw), dev(Gw)
+    plan.ns_step(l, g, 1)
+    plan.sync()
+    want_l, want_g = ons.ns_steps(Lw, Gw, 100.0, 1e-3, 1)
+    el, eg = relerr(l.cpu().numpy(), want_l), relerr(g.cpu().numpy(), want_g)
+    print('ns128 one step vs oracle: lambda %.2e, gamma %.2e' % (el, eg))
+    assert max(el, eg) <= TOL_SOLVE
+
+
 def test_ns_step_needs_every_solver_and_even_radial_grid(cyl):
     x = torch.zeros(8 * 12 * 9, dtype=torch.float64, device='cuda')
     noheat = cyl.Plan(12, 9, 8, 0.1, 1e-2, 1e-12, poisson=True, heat=False, extra_flags=cyl.WITH_DISK)
