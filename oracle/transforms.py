@@ -134,3 +134,77 @@ def vals2coeffs(f):
 def coeffs2vals(H):
     """Half-complex coefficients -> real values on the grid."""
     return coeffs2vals_complex(halfcomplex_to_complex(H)).real
+
+
+# ---------------------------------------------------------------- extended precision
+# The same direct sums in np.longdouble (64-bit mantissa on x86, 112 on
+# aarch64), with the matrices of the definitions built in that precision and
+# every phase reduced exactly in integers.  Used to write reference values
+# of computations whose FP64 rounding is amplified (the Navier-Stokes
+# nonlinear term), never by the checks of the transforms themselves.
+EXT = np.longdouble
+PI_EXT = EXT('3.14159265358979323846264338327950288419716939937510')
+
+
+def _cos_pi_ratio_ext(r, d):
+    """cos(pi r / d) in extended precision, reduced as in ``_cos_pi_ratio``."""
+    r = np.mod(np.asarray(r, dtype=np.int64), 2 * d)
+    r = np.where(r > d, 2 * d - r, r)
+    sign = np.where(2 * r > d, -1.0, 1.0).astype(EXT)
+    r = np.where(2 * r > d, d - r, r)
+    return sign * np.cos(PI_EXT * r.astype(EXT) / EXT(d))
+
+
+def _cheb_at_grid_ext(m):
+    N = m - 1
+    a = np.arange(m, dtype=np.int64)[:, None]
+    j = np.arange(m, dtype=np.int64)[None, :]
+    return _cos_pi_ratio_ext(j * (N - a), N)
+
+
+def _cheb_forward_matrix_ext(m):
+    V = _cheb_at_grid_ext(m)
+    w = np.ones(m, dtype=EXT)
+    w[0] = w[-1] = EXT(0.5)
+    return (EXT(2) / EXT(m - 1)) * (w[:, None] * (V * w[:, None]).T)
+
+
+def _fourier_halfcomplex_ext(p):
+    """Real matrices (F, I) of the theta stage in half-complex storage:
+    F maps values over l to (c_0, Re c_1, Im c_1, ..., c_{-p/2}) with
+    c_w = (1/p) sum_l f_l e^{-i w theta_l}; I maps them back,
+    f_l = c_0 + 2 sum_w (Re c_w cos w theta_l - Im c_w sin w theta_l)
+    + c_{-p/2} cos(p theta_l / 2) (theta_l = (2l - p) pi / p)."""
+    l = np.arange(p, dtype=np.int64)
+    F = np.zeros((p, p), dtype=EXT)
+    I = np.zeros((p, p), dtype=EXT)
+
+    def cos_sin(w):
+        r = w * (2 * l - p)                              # phase pi r / p
+        return _cos_pi_ratio_ext(r, p), _cos_pi_ratio_ext(2 * r - p, 2 * p)
+
+    c, _ = cos_sin(0)
+    F[0], I[:, 0] = c / p, c
+    for w in range(1, p // 2):
+        c, s = cos_sin(w)
+        F[2 * w - 1], F[2 * w] = c / p, -s / p
+        I[:, 2 * w - 1], I[:, 2 * w] = 2 * c, -2 * s
+    c, _ = cos_sin(-(p // 2))
+    F[p - 1], I[:, p - 1] = c / p, c
+    return F, I
+
+
+def vals2coeffs_ext(f):
+    """``vals2coeffs`` in extended precision (input and output np.longdouble)."""
+    p, m, n = f.shape
+    g = np.einsum('ja,lab->ljb', _cheb_forward_matrix_ext(m), f)
+    g = np.einsum('kb,ljb->ljk', _cheb_forward_matrix_ext(n), g)
+    return np.einsum('wl,ljk->wjk', _fourier_halfcomplex_ext(p)[0], g)
+
+
+def coeffs2vals_ext(H):
+    """``coeffs2vals`` in extended precision."""
+    p, m, n = H.shape
+    g = np.einsum('lw,wjk->ljk', _fourier_halfcomplex_ext(p)[1], H)
+    g = np.einsum('aj,ljk->lak', _cheb_at_grid_ext(m), g)
+    return np.einsum('bk,lak->lab', _cheb_at_grid_ext(n), g)

@@ -13,7 +13,10 @@ cylindrical formulas of the oracle fails:
 * the recovery of (lambda, gamma) from a PT field by the two horizontal
   solves (eq. ptpoisson);
 * quadratic scaling of the nonlinear term, and the linear limit of a step
-  (small amplitude: the step is the heat step of Section 3, eq. NSrewrite).
+  (small amplitude: the step is the heat step of Section 3, eq. NSrewrite);
+* the extended-precision path that writes reference values: its transforms
+  (round trip to 1e-17) and derivative matrix against the FP64 ones and
+  against exact values, the manufactured flow, agreement with the FP64 step.
 """
 import numpy as np
 import pytest
@@ -146,3 +149,52 @@ def test_nonlinear_term_is_quadratic_and_step_has_the_linear_limit():
 def test_odd_radial_grids_are_rejected():
     with pytest.raises(ValueError):
         ns.pt_components(np.zeros((4, 9, 5)), np.zeros((4, 9, 5)))
+
+
+EXT_BITS = np.finfo(np.longdouble).nmant
+needs_ext = pytest.mark.skipif(EXT_BITS < 63, reason='np.longdouble is not wider than double here')
+
+
+@needs_ext
+def test_extended_transforms_match_and_round_trip():
+    x = np.random.default_rng(11).standard_normal((10, 12, 9))
+    c = tr.vals2coeffs_ext(x.astype(tr.EXT))
+    assert _rel(np.asarray(c, dtype=np.float64), tr.vals2coeffs(x)) < 1e-15
+    assert np.abs(tr.coeffs2vals_ext(c) - x).max() < 1e-17 * np.abs(x).max()
+
+
+def test_exact_derivative_matrix():
+    M = ns.cheb_derivative_matrix_ext(9)
+    assert M[0, 3] == 3 and M[2, 3] == 6 and M[1, 3] == 0                 # T_3' = 12 x^2 - 3 = 6 T_2 + 3 T_0
+    assert M[1, 4] == 8 and M[3, 4] == 8 and M[0, 4] == 0                 # T_4' = 32 x^3 - 16 x = 8 T_3 + 8 T_1
+    C = np.eye(9)[None]                                                   # the FP64 matrix (D1, then C01 solve)
+    assert _rel(np.asarray(M, dtype=np.float64), ns.d_axis(C, 1)[0]) < 1e-14
+
+
+@needs_ext
+def test_extended_nonlinear_term_of_the_manufactured_flow():
+    lam_v, gam_v = LAM, GAM
+    lap = sp.diff(gam_v, xs, 2) + sp.diff(gam_v, ys, 2) + sp.diff(gam_v, zs, 2)
+    lam_w, gam_w = sp.expand(-lap), lam_v
+    v = _pt_cart(lam_v, gam_v)
+    w = _pt_cart(lam_w, gam_w)
+    Nc = (v[1] * w[2] - v[2] * w[1], v[2] * w[0] - v[0] * w[2], v[0] * w[1] - v[1] * w[0])
+    a = _curl(Nc)
+    Lw = tr.vals2coeffs(_vals(lam_w, P, M, N))
+    Gw = tr.vals2coeffs(_vals(gam_w, P, M, N))
+    # the same formulas as the FP64 path (the bar is set by the FP64 rounding of the input coefficients,
+    # which the derivatives amplify; the building blocks' own accuracy is pinned above)
+    _, _, s1, s2 = ns.nonlinear_pt(Lw, Gw, return_rhs=True, extended=True)
+    assert _rel(tr.coeffs2vals(s1), _vals(a[2], P, M, N)) < 1e-10
+    assert _rel(tr.coeffs2vals(s2), _vals(_curl(a)[2], P, M, N)) < 1e-10
+
+
+@needs_ext
+def test_extended_step_agrees_with_the_fp64_step():
+    from paper_2206_04827_gb300 import inputs
+    rng = np.random.default_rng(5)
+    Lw = 3.0 * inputs.smooth_coeffs(8, 12, 11, 1.4, rng)
+    Gw = 3.0 * inputs.smooth_coeffs(8, 12, 11, 1.4, rng)
+    l64, g64 = ns.ns_steps(Lw, Gw, 20.0, 5e-3, 2)
+    lx, gx = ns.ns_steps(Lw, Gw, 20.0, 5e-3, 2, extended=True)
+    assert _rel(lx, l64) < 1e-12 and _rel(gx, g64) < 1e-12
