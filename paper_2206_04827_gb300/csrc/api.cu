@@ -1099,8 +1099,19 @@ cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kN
     if ((ee = d('t', gam, W[7])) != cudaSuccess || (ee = d('t', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
     return acc(Vz, W[8], -1.0, -2, false);
   };
-  // 1. velocity potentials (eq. ptcurl): lambda_v = gamma_w, -lap gamma_v = lambda_w
-  NS_S(run_adi(P, 0, lw, W[0], nullptr, 0.0, 0, 1, nullptr, 1));
+  // 1. velocity potentials (eq. ptcurl): lambda_v = gamma_w, -lap gamma_v = lambda_w, refined once: the
+  //    first solution u1 (W[1]) enters as the lifting of a second solve whose right side is the
+  //    residual (W[2] = minus the Poisson operator applied to u1), so W[0] = u1 + the correction.  The
+  //    nonlinear term differentiates gamma_v up to three times; at 128^3 the ADI's own error (~2e-14
+  //    of max|gamma_v|) alone moved a step by ~4e-11.
+  NS_S(run_adi(P, 0, lw, W[1], nullptr, 0.0, 0, 1, nullptr, 1));
+  {
+    cyl::AdiArgs a = step_args(P, 0, lw, W[0], nullptr, 0.0, 0, 1, nullptr, 1, false);
+    NS_TRY(cyl::launch_lift_correction(a, W[1], W[2], 0.0, 1.0, std::min(P->threads[0], 256), st));
+    a.lift = W[1];
+    a.corr = W[2];
+    NS_TRY(cyl::launch_adi(a, P->threads[0], P->smem[0], st));
+  }
   // 2. v and omega on the grid (eq. pt)
   NS_S(pt_field(gw, W[0], W[1], W[2], W[3]));
   NS_S(pt_field(lw, gw, W[4], W[5], W[6]));
