@@ -61,6 +61,7 @@ UNIT = 'unknowns\u00b7steps/s'
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2      # the FP64 pipe's issue rate, confirmed live by cyl_fp64_fma_probe
 GOLD512 = os.path.join(ROOT, 'tests', 'golden', 'large512_sampled.npz')
+GOLDNS = os.path.join(ROOT, 'tests', 'golden', 'ns128_sampled.npz')
 
 
 # sources that decide the ADI kernels' code, tables and launch layout
@@ -803,13 +804,14 @@ class NS128(Workload):
         self.Lw, self.Gw = torch.empty_like(self.L0), torch.empty_like(self.G0)
         self.ws = torch.empty((self.plan.ns_workspace_bytes() + 7) // 8, dtype=torch.float64, device=dev)
         self.units = L ** 3 * self.STEPS
-        # FP64 flops of a step: the ADI solves (one Poisson solve, two heat steps) and the 28 chirp-z
-        # transforms (22 coefficient -> value, 6 value -> coefficient; flops as in the xform workloads)
+        # FP64 flops of a step: the ADI solves (one Poisson solve, two heat steps; the refinement solve of
+        # the Poisson step is not counted) and the 26 chirp-z transforms (20 coefficient -> value,
+        # 6 value -> coefficient; flops as in the xform workloads)
         info, _ = cyl.xform_table(0, L)
         per_line = 10 * info['P'] * info['logP'] + 12 * info['P']
-        xflops = 28 * per_line * (2 * L * L + L * L / 2.0)
+        xflops = 26 * per_line * (2 * L * L + L * L / 2.0)
         self.flops = self.STEPS * (self.plan.flops(0, 1) + 2 * self.plan.flops(1, 1) + xflops)
-        self.launches = self.STEPS * 150
+        self.launches = self.STEPS * 146
         self.kernel = 'chirp_xform_kernel + adi_kernel'
         self.config = {'workload': 'Navier-Stokes 128^3 (poloidal-toroidal vorticity, IMEX BDF1), Re 100, dt 1e-3, '
                                    '%d steps from smooth seeded potentials' % self.STEPS,
@@ -822,6 +824,27 @@ class NS128(Workload):
 
     def step(self):
         self.plan.ns_step(self.Lw, self.Gw, self.STEPS, workspace=self.ws)
+
+    def accuracy(self):
+        """One step from the seeded potentials against the extended-precision
+        reference values of that step (sampled slices and coefficients); the
+        bar is 4x the FP64 oracle's own distance from them."""
+        t = self.torch
+        ref = np.load(GOLDNS)
+        l, g = self.L0.clone(), self.G0.clone()
+        self.plan.ns_step(l, g, 1, workspace=self.ws)
+        sl = t.as_tensor(ref['slices'], device=l.device)
+        idx = t.as_tensor(ref['idx'], device=l.device)
+        pick = lambda X: X.index_select(0, sl).index_select(1, idx).index_select(2, idx).cpu().numpy()
+        el = float(np.abs(pick(l) - ref['lam']).max() / float(ref['lam_max']))
+        eg = float(np.abs(pick(g) - ref['gam']).max() / float(ref['gam_max']))
+        return {'max_rel_err_vs_oracle': max(el, eg),
+                'accuracy_detail': {'lambda_one_step': el, 'gamma_one_step': eg,
+                                    'fp64_oracle_floor': {'lambda': float(ref['fp64_err_lam']),
+                                                          'gamma': float(ref['fp64_err_gam'])},
+                                    'reference': 'extended-precision oracle step on %d slices x %d x %d '
+                                                 'coefficients (tests/golden/ns128_sampled.npz)'
+                                                 % (len(ref['slices']), len(ref['idx']), len(ref['idx']))}}
 
     def e2e_setup(self):
         t = self.torch

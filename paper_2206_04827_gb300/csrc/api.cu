@@ -1081,8 +1081,11 @@ cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kN
   };
 #define NS_TRY(x) do { if ((e = (x)) != cudaSuccess) return from_cuda(e); } while (0)
 #define NS_S(x) do { if ((s = (x)) != CYL_OK) return s; } while (0)
-  // PT components of curl(lam z) + curl curl(gam z) into (Vr, Vt, Vz), grid values (eq. pt)
-  auto pt_field = [&](const double *lam, const double *gam, double *Vr, double *Vt, double *Vz) -> cyl_status {
+  // PT components of curl(lam z) + curl curl(gam z) into (Vr, Vt, Vz), grid values (eq. pt).  The
+  // values of d_r lam are kept in dr_lam_out when given; dr_gam_in, when given, holds the values of
+  // d_r gam (the velocity's lambda is the vorticity's gamma, so the second call reuses the first's).
+  auto pt_field = [&](const double *lam, const double *gam, double *Vr, double *Vt, double *Vz, double *dr_lam_out,
+                      const double *dr_gam_in) -> cyl_status {
     cyl_status q;
     cudaError_t ee;
     if ((ee = d('t', lam, W[7])) != cudaSuccess) return from_cuda(ee);          // V_r = r^-1 d_th lam + d_r d_z gam
@@ -1090,12 +1093,23 @@ cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kN
     if ((ee = d('z', gam, W[7])) != cudaSuccess || (ee = d('r', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
     if ((q = acc(Vr, W[8], 1.0, 0, false)) != CYL_OK) return q;
     if ((ee = d('r', lam, W[7])) != cudaSuccess) return from_cuda(ee);          // V_th = -d_r lam + r^-1 d_th d_z gam
-    if ((q = acc(Vt, W[7], -1.0, 0, true)) != CYL_OK) return q;
+    if (dr_lam_out) {
+      if ((q = coeffs2vals_impl(P, W[7], dr_lam_out)) != CYL_OK) return q;
+      if ((ee = cyl::launch_accum_r(Vt, dr_lam_out, P->d_radius, p, m, n, -1.0, 0, true, sms, st)) != cudaSuccess)
+        return from_cuda(ee);
+    } else if ((q = acc(Vt, W[7], -1.0, 0, true)) != CYL_OK) {
+      return q;
+    }
     if ((ee = d('z', gam, W[7])) != cudaSuccess || (ee = d('t', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
     if ((q = acc(Vt, W[8], 1.0, -1, false)) != CYL_OK) return q;
     if ((ee = d('r', gam, W[7])) != cudaSuccess || (ee = d('r', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
     if ((q = acc(Vz, W[8], -1.0, 0, true)) != CYL_OK) return q;                 // V_z = -Delta_h gam
-    if ((q = acc(Vz, W[7], -1.0, -1, false)) != CYL_OK) return q;
+    if (dr_gam_in) {
+      if ((ee = cyl::launch_accum_r(Vz, dr_gam_in, P->d_radius, p, m, n, -1.0, -1, false, sms, st)) != cudaSuccess)
+        return from_cuda(ee);
+    } else if ((q = acc(Vz, W[7], -1.0, -1, false)) != CYL_OK) {
+      return q;
+    }
     if ((ee = d('t', gam, W[7])) != cudaSuccess || (ee = d('t', W[7], W[8])) != cudaSuccess) return from_cuda(ee);
     return acc(Vz, W[8], -1.0, -2, false);
   };
@@ -1112,9 +1126,9 @@ cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kN
     a.corr = W[2];
     NS_TRY(cyl::launch_adi(a, P->threads[0], P->smem[0], st));
   }
-  // 2. v and omega on the grid (eq. pt)
-  NS_S(pt_field(gw, W[0], W[1], W[2], W[3]));
-  NS_S(pt_field(lw, gw, W[4], W[5], W[6]));
+  // 2. v and omega on the grid (eq. pt); W[10] carries the values of d_r gamma_w from one to the other
+  NS_S(pt_field(gw, W[0], W[1], W[2], W[3], W[10], nullptr));
+  NS_S(pt_field(lw, gw, W[4], W[5], W[6], nullptr, W[10]));
   // 3. N = v x omega (in place of v)
   {
     const double *V[3] = {W[1], W[2], W[3]}, *Om[3] = {W[4], W[5], W[6]};
@@ -1137,12 +1151,12 @@ cyl_status ns_one_step(cyl_plan_s *P, double *lw, double *gw, double *const W[kN
   NS_TRY(d('t', W[5], W[7]));
   NS_S(acc(W[11], W[7], 1.0, -1, false));
   NS_S(vals2coeffs_impl(P, W[11], W[8]));
-  NS_TRY(d('z', W[8], W[7]));
+  NS_TRY(d('z', W[8], W[7]));                      // the two r^0 terms combined in coefficients:
+  NS_TRY(d('r', W[6], W[8]));                      // W[7] = d_z div_h - d_r^2 N_z, one transform
+  NS_TRY(d('r', W[8], W[9]));
+  NS_TRY(cyl::launch_accum_r(W[7], W[9], P->d_radius, p, m, n, -1.0, 0, false, sms, st));
   NS_S(coeffs2vals_impl(P, W[7], W[11]));
-  NS_TRY(d('r', W[6], W[7]));
-  NS_TRY(d('r', W[7], W[8]));
-  NS_S(acc(W[11], W[8], -1.0, 0, false));
-  NS_S(acc(W[11], W[7], -1.0, -1, false));
+  NS_S(acc(W[11], W[8], -1.0, -1, false));
   NS_TRY(d('t', W[6], W[7]));
   NS_TRY(d('t', W[7], W[8]));
   NS_S(acc(W[11], W[8], -1.0, -2, false));
