@@ -349,7 +349,7 @@ class Workload:
 class Heat128(Workload):
     name = 'heat128'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch of the bench
-    TRAFFIC = (49169920 + 1013504, '722528673eaf')
+    TRAFFIC = (49200128 + 1032192, '3db055c5db6d')
     TRAFFIC_BASIS = 'ncu capture of the bench launch'
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
@@ -472,9 +472,9 @@ class Poisson33(Workload):
 class Large512(Workload):
     name = 'large512'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches on the same
-    # workload with n_theta = 320 (Poisson 36,376,811,520 + 41,409,028,608; 20 heat steps
-    # 616,543,005,952 + 647,541,979,648), scaled to n_theta = 512 by the items processed
-    TRAFFIC = (36376811520 + 41409028608 + 616543005952 + 647541979648, '722528673eaf')
+    # workload with n_theta = 320 (Poisson 36,252,707,328 + 41,344,285,952; 20 heat steps
+    # 615,971,362,816 + 645,704,382,464), scaled to n_theta = 512 by the items processed
+    TRAFFIC = (36252707328 + 41344285952 + 615971362816 + 645704382464, '3db055c5db6d')
     TRAFFIC_BASIS = 'ncu capture of the step at n_theta = 320 (two launches), scaled by 512 / 320'
     TRAFFIC_NTHETA = 320
 
@@ -811,7 +811,7 @@ class NS128(Workload):
         per_line = 10 * info['P'] * info['logP'] + 12 * info['P']
         xflops = 26 * per_line * (2 * L * L + L * L / 2.0)
         self.flops = self.STEPS * (self.plan.flops(0, 1) + 2 * self.plan.flops(1, 1) + xflops)
-        self.launches = self.STEPS * 146
+        self.launches = self.STEPS * 138
         self.kernel = 'chirp_xform_kernel + adi_kernel'
         self.config = {'workload': 'Navier-Stokes 128^3 (poloidal-toroidal vorticity, IMEX BDF1), Re 100, dt 1e-3, '
                                    '%d steps from smooth seeded potentials' % self.STEPS,
