@@ -349,7 +349,7 @@ class Workload:
 class Heat128(Workload):
     name = 'heat128'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch of the bench
-    TRAFFIC = (49200128 + 1032192, '3db055c5db6d')
+    TRAFFIC = (49316608 + 977664, '66b2db0074ff')
     TRAFFIC_BASIS = 'ncu capture of the bench launch'
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
@@ -472,9 +472,9 @@ class Poisson33(Workload):
 class Large512(Workload):
     name = 'large512'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches on the same
-    # workload with n_theta = 320 (Poisson 36,252,707,328 + 41,344,285,952; 20 heat steps
-    # 615,971,362,816 + 645,704,382,464), scaled to n_theta = 512 by the items processed
-    TRAFFIC = (36252707328 + 41344285952 + 615971362816 + 645704382464, '3db055c5db6d')
+    # workload with n_theta = 320 (Poisson 34,195,699,200 + 35,829,435,648; 20 heat steps
+    # 576,059,499,520 + 558,830,722,304), scaled to n_theta = 512 by the items processed
+    TRAFFIC = (34195699200 + 35829435648 + 576059499520 + 558830722304, '66b2db0074ff')
     TRAFFIC_BASIS = 'ncu capture of the step at n_theta = 320 (two launches), scaled by 512 / 320'
     TRAFFIC_NTHETA = 320
 
