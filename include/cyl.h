@@ -70,8 +70,10 @@ typedef enum {
  * a stream capture does not allow) */
 #define CYL_WITH_BC       64u
 /* plain LU sweeps only: no twisted (two-sided) solves, which otherwise run
- * where every sweep has at most 128 chains (grids up to about 130); the
- * results then match the persistent batch kernel bit for bit */
+ * where every sweep of a two-slice item has at most 128 chains (grids up to
+ * about 130) and, with single-slice items, where two-slice work arrays leave
+ * shared memory (grids of about 220 to 514 points per axis); the results
+ * then match the persistent batch kernel bit for bit */
 #define CYL_PLAIN_SWEEPS 128u
 /* build the horizontal (disk) Poisson tables for cyl_disk_poisson */
 #define CYL_WITH_DISK    256u
