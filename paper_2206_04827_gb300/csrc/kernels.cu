@@ -187,24 +187,21 @@ __device__ __forceinline__ void radial_sweep(double *__restrict__ col, const dou
   }
 }
 
-// One-sided vertical sweep of one row; the row values are read four columns
-// ahead into named registers, as in the twisted sweeps below (with the work
-// arrays in global memory each new 32-byte sector of a row is then in flight
-// while the previous one is used: 512^3 with two-slice items 0.60 -> 0.62).
 template <bool LAST, int UNR>
 __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const double *__restrict__ ZB, int Nz) {
   constexpr int ALO = 1;                                    // apply offsets [-1, 2]
   const double2 *z2p = reinterpret_cast<const double2 *>(ZB);
   double wq = 0.0;
-  double q0 = row[0], q1 = 1 < Nz ? row[1] : 0.0, q2 = 2 < Nz ? row[2] : 0.0, q3 = 3 < Nz ? row[3] : 0.0;
+  double rn = row[0];
   double2 cn = z2p[0];
 #pragma unroll UNR
   for (int b = 0; b < Nz; ++b) {
-    const double r = q0;
-    q0 = q1; q1 = q2; q2 = q3;
-    q3 = (b + 4 < Nz) ? row[b + 4] : 0.0;
+    const double r = rn;
     const double2 c = cn;
-    if (b + 1 < Nz) cn = z2p[(b + 1) * 4];
+    if (b + 1 < Nz) {
+      rn = row[b + 1];
+      cn = z2p[(b + 1) * 4];
+    }
     const double w = fma(c.x, wq, r);                       // [0] -L[c][c-1]
     row[b] = w;
     wq = w;
@@ -212,18 +209,16 @@ __device__ __forceinline__ void vertical_sweep(double *__restrict__ row, const d
   double x1 = 0.0, x2 = 0.0, x3 = 0.0;                      // x_{b+1}, x_{b+2}, x_{b+3}
   double2 p01 = z2p[(Nz - 1) * 4], p23 = z2p[(Nz - 1) * 4 + 1], p45, p67;
   if (!LAST) { p45 = z2p[(Nz - 1) * 4 + 2]; p67 = z2p[(Nz - 1) * 4 + 3]; }
-  double w0 = row[Nz - 1], w1 = Nz - 2 >= 0 ? row[Nz - 2] : 0.0, w2 = Nz - 3 >= 0 ? row[Nz - 3] : 0.0,
-         w3 = Nz - 4 >= 0 ? row[Nz - 4] : 0.0;
+  double wn = row[Nz - 1];
   double2 q45 = make_double2(0.0, 0.0), q67 = make_double2(0.0, 0.0);   // apply record of column b+1
 #pragma unroll UNR
   for (int b = Nz - 1; b >= 0; --b) {
-    const double wb = w0;
-    w0 = w1; w1 = w2; w2 = w3;
-    w3 = (b - 4 >= 0) ? row[b - 4] : 0.0;
+    const double wb = wn;
     const double2 c01 = p01, c23 = p23;
     double2 c45, c67;
     if (!LAST) { c45 = p45; c67 = p67; }
     if (b > 0) {
+      wn = row[b - 1];
       p01 = z2p[(b - 1) * 4];
       p23 = z2p[(b - 1) * 4 + 1];
       if (!LAST) { p45 = z2p[(b - 1) * 4 + 2]; p67 = z2p[(b - 1) * 4 + 3]; }
