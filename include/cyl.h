@@ -495,12 +495,15 @@ cyl_status cyl_plan_operator(cyl_plan_t plan, int op, int which, int k, int pari
                              double *out);
 
 /* Launch layout of one kind's ADI kernel (which as above; plans only, not
- * batch plans: CYL_ESTATE).  info[8] receives {items, threads per CTA,
+ * batch plans: CYL_ESTATE).  info[9] receives {items, threads per CTA,
  * twisted half (threads per side of a twisted solve, 0: one-sided sweeps),
  * placement (2: iterate and right side in shared memory, 1: iterate only,
  * 0: both in the per-item global work area), dynamic shared memory bytes,
  * CTAs per item (1, or the cluster size in cluster mode), slices per item
- * (the largest), built (0 when the kind was not built)}.  Items whose two
+ * (the largest), built (0 when the kind was not built), all twisted (1 when
+ * every item's forward solves are twisted both ways: with the work arrays in
+ * global memory the launch then uses a kernel compiled without the
+ * one-sided sweeps)}.  Items whose two
  * slices leave shared memory are split into single-slice items with twisted
  * solves on two threads per chain (up to 2 x 256 threads), unless
  * CYL_PLAIN_SWEEPS or cluster mode is given. */

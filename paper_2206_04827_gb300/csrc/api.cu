@@ -29,6 +29,8 @@ struct cyl_plan_s {
   size_t smem[cyl::kNumKinds] = {};
   int use_smem[cyl::kNumKinds] = {1, 1, 1, 1, 1};
   int twist_half[cyl::kNumKinds] = {};   // > 0: the kind's tables hold twisted solves
+  int all_tw[cyl::kNumKinds] = {};       // every item twisted both ways (forward / transposed records)
+  int all_twT[cyl::kNumKinds] = {};
   int cluster = 0;                        // > 1: CTAs per item of the cluster-mode ADI launch
   int ld = 1, smem_rows = 0, maxM = 0, maxNz = 0;
   long long gwork_per_item = 0;
@@ -161,6 +163,7 @@ cyl::AdiArgs adi_args(cyl_plan_s *P, int kind) {
   a.err = P->d_err;
   a.twist_half = P->twist_half[kind];
   a.cluster = P->cluster;
+  a.all_twisted = P->cluster > 1 ? 0 : P->all_tw[kind];
   a.ckpt_every = 1;
   a.test_no_tma = (P->hp.flags & CYL_TEST_NO_TMA) ? 1 : 0;
   a.wait_limit = a.test_no_tma ? kTestWaitCycles : kWaitCycles;
@@ -459,6 +462,13 @@ cyl_status cyl_plan_bdf(cyl_plan_t *plan, int n_r, int n_z, int n_theta, double 
     // twisted solves: one thread per chain and side (top chains in the first half)
     const int half = (thr + 31) / 32 * 32;
     P->twist_half[kind] = tw ? half : 0;
+    bool all = !h.kind[kind].items.empty(), allT = all;
+    for (const Item &it : h.kind[kind].items) {
+      all = all && it.twr > 0 && it.twz > 0;
+      allT = allT && it.twrT > 0 && it.twzT > 0 && it.roffT >= 0 && it.zoffT >= 0;
+    }
+    P->all_tw[kind] = all ? 1 : 0;
+    P->all_twT[kind] = allT ? 1 : 0;
     // one-sided sweeps: one thread per chain up to 512; the threads loop over further chains
     P->threads[kind] = tw ? 2 * half : std::min(half, 512);
     const int th = P->twist_half[kind];
@@ -757,6 +767,7 @@ cyl_status cyl_heat_adjoint_bdf(cyl_plan_t P, const double *hist0, int nvalid, c
       adj.n_lo = s_lo;
       adj.n_hi = s_hi;
       cyl::AdiArgs a = adi_args(P, b);
+      a.all_twisted = P->cluster > 1 ? 0 : P->all_twT[b];
       cudaError_t err = cyl::launch_adjoint(a, adj, P->threads[b], P->smem[b], P->st);
       if (err != cudaSuccess) return from_cuda(err);
       s_hi = s_lo;
@@ -857,6 +868,7 @@ cyl_status cyl_heat_adjoint_bc(cyl_plan_t P, const double *T0, const double *g, 
     return CYL_OK;
   }
   cyl::AdiArgs a = adi_args(P, 1);
+  a.all_twisted = P->cluster > 1 ? 0 : P->all_twT[1];
   cyl::AdjointArgs adj{};
   adj.lam = dL_dT0;
   adj.G = g;
@@ -992,6 +1004,7 @@ cyl_status cyl_plan_launch_info(cyl_plan_t P, int which, int *info) {
   info[5] = P->cluster > 1 ? P->cluster : 1;
   info[6] = nsl;
   info[7] = KT.built ? 1 : 0;
+  info[8] = (P->cluster > 1 || !KT.built) ? 0 : P->all_tw[which];
   return CYL_OK;
 }
 

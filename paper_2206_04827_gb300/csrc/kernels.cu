@@ -473,12 +473,13 @@ __device__ __forceinline__ void radial_tw2(double *__restrict__ col, int ld, con
 // Vertical phase 1: top: save z_k, z_{k+1}, forward LU columns 0 .. k-1;
 // bottom: forward UL columns Nz-1 .. k+2.  In place on row.  The vertical
 // sweeps walk one row per thread, so each step's load is a separate 32-byte
-// sector per thread; the row values are read four columns ahead into a
-// queue of named registers (q0 .. q3), which keeps a sector's load in flight
-// across the steps that use the previous one.  Measured on GB300 at 512^3
-// with the work arrays in global memory: 0.79 / 0.76 of the FP64 peak
-// (Poisson / heat) against 0.67 with one column of look-ahead; an indexed
-// array queue let the compiler sink the loads and lost the gain.
+// sector per thread; the row values are read six columns ahead into a queue
+// of named registers (q0 .. q5), which keeps the next sectors' loads in
+// flight across the steps that use the previous one.  Measured on GB300 at
+// 512^3 with the work arrays in global memory (all-twisted kernel): 0.81 /
+// 0.80 of the FP64 peak (Poisson / heat) against 0.67 with one column of
+// look-ahead and 0.79 / 0.76 with four; an indexed-array queue let the
+// compiler sink the loads and lost the gain.
 template <int UNR>
 __device__ __forceinline__ void vertical_tw1(double *__restrict__ row, const double *__restrict__ ZB, int Nz, int k,
                                              bool bottom, double *__restrict__ xs, int xst) {
@@ -487,13 +488,14 @@ __device__ __forceinline__ void vertical_tw1(double *__restrict__ row, const dou
     xs[xst] = row[k];
     xs[2 * xst] = row[k + 1];
     double wq = 0.0;
-    double q0 = row[0], q1 = 1 < k ? row[1] : 0.0, q2 = 2 < k ? row[2] : 0.0, q3 = 3 < k ? row[3] : 0.0;
+    double q0 = 0 < k ? row[0] : 0.0, q1 = 1 < k ? row[1] : 0.0, q2 = 2 < k ? row[2] : 0.0, q3 = 3 < k ? row[3] : 0.0,
+           q4 = 4 < k ? row[4] : 0.0, q5 = 5 < k ? row[5] : 0.0;
     double2 cn = z2p[0];
 #pragma unroll UNR
     for (int b = 0; b < k; ++b) {
       const double r = q0;
-      q0 = q1; q1 = q2; q2 = q3;
-      q3 = (b + 4 < k) ? row[b + 4] : 0.0;
+      q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5;
+      q5 = (b + 6 < k) ? row[b + 6] : 0.0;
       const double2 cc = cn;
       if (b + 1 < k) cn = z2p[(b + 1) * 4];
       const double w = fma(cc.x, wq, r);
@@ -503,14 +505,15 @@ __device__ __forceinline__ void vertical_tw1(double *__restrict__ row, const dou
     xs[0] = wq;          // w_{k-1}
   } else {
     double v1 = 0.0, v2 = 0.0;
-    double q0 = row[Nz - 1], q1 = Nz - 2 >= k + 2 ? row[Nz - 2] : 0.0, q2 = Nz - 3 >= k + 2 ? row[Nz - 3] : 0.0,
-           q3 = Nz - 4 >= k + 2 ? row[Nz - 4] : 0.0;
+    double q0 = Nz - 1 >= k + 2 ? row[Nz - 1] : 0.0, q1 = Nz - 2 >= k + 2 ? row[Nz - 2] : 0.0,
+           q2 = Nz - 3 >= k + 2 ? row[Nz - 3] : 0.0, q3 = Nz - 4 >= k + 2 ? row[Nz - 4] : 0.0,
+           q4 = Nz - 5 >= k + 2 ? row[Nz - 5] : 0.0, q5 = Nz - 6 >= k + 2 ? row[Nz - 6] : 0.0;
     double2 cn = z2p[(Nz - 1) * 4];
 #pragma unroll UNR
     for (int b = Nz - 1; b >= k + 2; --b) {
       const double r = q0;
-      q0 = q1; q1 = q2; q2 = q3;
-      q3 = (b - 4 >= k + 2) ? row[b - 4] : 0.0;
+      q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5;
+      q5 = (b - 6 >= k + 2) ? row[b - 6] : 0.0;
       const double2 cc = cn;
       if (b - 1 >= k + 2) cn = z2p[(b - 1) * 4];
       const double v = fma(cc.x, v1, fma(cc.y, v2, r));   // -Ut[b][b+1], -Ut[b][b+2]
@@ -549,15 +552,15 @@ __device__ __forceinline__ void vertical_tw2(double *__restrict__ row, const dou
       row[k + 1] = xI[1];
     }
     double2 q45 = z2p[k * 4 + 2], q67 = z2p[k * 4 + 3];    // apply record of column b+1
-    double q0 = row[k - 1], q1 = k - 2 >= 0 ? row[k - 2] : 0.0, q2 = k - 3 >= 0 ? row[k - 3] : 0.0,
-           q3 = k - 4 >= 0 ? row[k - 4] : 0.0;
+    double q0 = k - 1 >= 0 ? row[k - 1] : 0.0, q1 = k - 2 >= 0 ? row[k - 2] : 0.0, q2 = k - 3 >= 0 ? row[k - 3] : 0.0,
+           q3 = k - 4 >= 0 ? row[k - 4] : 0.0, q4 = k - 5 >= 0 ? row[k - 5] : 0.0, q5 = k - 6 >= 0 ? row[k - 6] : 0.0;
     double2 p01 = z2p[(k - 1) * 4], p23 = z2p[(k - 1) * 4 + 1], p45, p67;
     if (!LAST) { p45 = z2p[(k - 1) * 4 + 2]; p67 = z2p[(k - 1) * 4 + 3]; }
 #pragma unroll UNR
     for (int b = k - 1; b >= 0; --b) {
       const double wb = q0;
-      q0 = q1; q1 = q2; q2 = q3;
-      q3 = (b - 4 >= 0) ? row[b - 4] : 0.0;
+      q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5;
+      q5 = (b - 6 >= 0) ? row[b - 6] : 0.0;
       const double2 c01 = p01, c23 = p23;
       double2 c45, c67;
       if (!LAST) { c45 = p45; c67 = p67; }
@@ -591,14 +594,14 @@ __device__ __forceinline__ void vertical_tw2(double *__restrict__ row, const dou
     }
   } else {
     double xm3 = 0.0, xm2 = xI[0], xm1 = xI[1];            // x_{b-3}, x_{b-2}, x_{b-1}
-    double q0 = row[k + 2], q1 = k + 3 < Nz ? row[k + 3] : 0.0, q2 = k + 4 < Nz ? row[k + 4] : 0.0,
-           q3 = k + 5 < Nz ? row[k + 5] : 0.0;
+    double q0 = k + 2 < Nz ? row[k + 2] : 0.0, q1 = k + 3 < Nz ? row[k + 3] : 0.0, q2 = k + 4 < Nz ? row[k + 4] : 0.0,
+           q3 = k + 5 < Nz ? row[k + 5] : 0.0, q4 = k + 6 < Nz ? row[k + 6] : 0.0, q5 = k + 7 < Nz ? row[k + 7] : 0.0;
     double2 p23 = z2p[(k + 2) * 4 + 1];
 #pragma unroll UNR
     for (int b = k + 2; b < Nz; ++b) {
       const double vb = q0;
-      q0 = q1; q1 = q2; q2 = q3;
-      q3 = (b + 4 < Nz) ? row[b + 4] : 0.0;
+      q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5;
+      q5 = (b + 6 < Nz) ? row[b + 6] : 0.0;
       const double2 c23 = p23;
       if (b + 1 < Nz) p23 = z2p[(b + 1) * 4 + 1];
       const double xb = fma(c23.x, xm1, c23.y * vb);       // -Lt[b][b-1]/Lt_bb, 1/Lt_bb
@@ -689,7 +692,12 @@ __device__ __forceinline__ void issue_tables(const AdiShared &sh, const AdiArgs 
 // TW: compiled with the twisted sweeps (items whose tables carry twisted
 // solves, twr / twz > 0); without it only the one-sided sweeps are compiled,
 // which keeps the register allocation of the plain kernels unchanged.
-template <bool TT, int UNR, bool TW = false>
+// OTW: every item of the launch is twisted in both directions (the host
+// checks): the one-sided sweeps are not compiled at all, which leaves the
+// 128 registers of a 512-thread CTA to the twisted sweeps and their
+// six-column queue (measured at 512^3: 0.81 / 0.80 of the FP64 peak, Poisson
+// / heat, against 0.78 / 0.77 with the one-sided sweeps compiled in).
+template <bool TT, int UNR, bool TW = false, bool OTW = false>
 __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &sh, const AdiArgs &a, const Item &it,
                                                double *S, const double *Fa, int ldF, long long &c, long long c0,
                                                long long c_end, bool &timed_out) {
@@ -709,7 +717,7 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
     const bool bottom = gp.tid >= xh;
     const int chain = gp.tid - (bottom ? xh : 0);
     const int twr = TT ? it.twrT : it.twr, twz = TT ? it.twzT : it.twz;
-    if (TW && twr) {
+    if (OTW || (TW && twr)) {
       const int col = cb0 + chain;
       if (col < cb1) {
         if (jt == 0) radial_tw1<true, UNR>(S + col, Fa + col, ld, RB, M, twr, bottom, sh.xs + chain, xh);
@@ -717,14 +725,14 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
       }
       gp.sync();
       if (col < cb1) radial_tw2<UNR>(S + col, ld, RB, M, twr, bottom, sh.xs + chain, xh);
-    } else {
+    } else if constexpr (!OTW) {
       for (int col = cb0 + gp.tid; col < cb1; col += gp.nth) {
         if (jt == 0) radial_sweep<true, UNR>(S + col, Fa + col, ld, RB, M);
         else radial_sweep<false, UNR>(S + col, Fa + col, ld, RB, M);
       }
     }
     gp.csync();
-    if (TW && twz) {
+    if (OTW || (TW && twz)) {
       const int r = rb0 + chain;
       const int sl = r / M, aa = r - sl * M;
       double *rowp = S + aa * ld + sl * Nz;
@@ -734,7 +742,7 @@ __device__ __forceinline__ void adi_iterations(const Grp &gp, const AdiShared &s
         if (jt + 1 == J) vertical_tw2<true, UNR>(rowp, ZB, Nz, twz, bottom, sh.xs + chain, xh);
         else vertical_tw2<false, UNR>(rowp, ZB, Nz, twz, bottom, sh.xs + chain, xh);
       }
-    } else {
+    } else if constexpr (!OTW) {
       for (int r = rb0 + gp.tid; r < rb1; r += gp.nth) {
         const int sl = r / M, aa = r - sl * M;
         if (jt + 1 == J) vertical_sweep<true, UNR>(S + aa * ld + sl * Nz, ZB, Nz);
@@ -756,7 +764,7 @@ __device__ __forceinline__ void init_bars(const Grp &gp, unsigned long long *bar
 }
 
 // Every BDF1 step of one item (see adi_kernel): right side, ADI, expansion.
-template <int UNR, bool TW = false>
+template <int UNR, bool TW = false, bool OTW = false>
 __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArgs &a, const Item &it,
                                                      const AdiShared &sh, double *S, double *Fa, long long &c,
                                                      bool &timed_out) {
@@ -831,7 +839,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
     }
     gp.sync();
 
-    adi_iterations<false, UNR, TW>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
+    adi_iterations<false, UNR, TW, OTW>(gp, sh, a, it, S, Fa, ld, c, c0, c_end, timed_out);
 
     // X = S_r Y S_z^T on this item's class rows / columns (phi_j = T_{j+2} - T_j).
     const int Wf = nsl * it.Nzfull, f0 = gp.lo(Wf), Wfp = gp.hi(Wf) - f0;
@@ -871,7 +879,7 @@ __device__ __forceinline__ void process_item_forward(const Grp &gp, const AdiArg
 
 // One CTA per item.  S_SMEM / F_SMEM place the item's iterate (S) and right
 // side (Fa) in shared memory, else in the per-item global work area.
-template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW, bool OTW = false>
 __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -894,7 +902,7 @@ __global__ void __launch_bounds__(MAXT, 1) adi_kernel(const AdiArgs a) {
   init_bars(gp, bar);
   bool timed_out = false;
   long long c = 0;
-  process_item_forward<S_SMEM ? 2 : 8, TW>(gp, a, it, sh, S, Fa, c, timed_out);
+  process_item_forward<S_SMEM ? 2 : 8, TW, OTW>(gp, a, it, sh, S, Fa, c, timed_out);
   if (timed_out && a.err) atomicExch(a.err, (int)CYL_ERR_TIMEOUT);
 }
 
@@ -1060,7 +1068,7 @@ cudaError_t launch_batch(const AdiArgs &a, int *queue, int G, int threads, int b
 // rows and, per slice, the class columns), so mu is written and Lambda read
 // in reversed order and the forward sweeps (twisted where the records are)
 // do the iterations with the transposed records.  Work arrays as adi_kernel.
-template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW, bool OTW = false>
 __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, AdjointArgs g) {
   extern __shared__ __align__(16) double sm[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -1107,7 +1115,7 @@ __global__ void __launch_bounds__(MAXT, 1) adi_adjoint_kernel(const AdiArgs a, A
       Fa[(M - 1 - aa) * ld + sl * Nz + (Nz - 1 - b)] = lin[o] - lin[o + 2] - lin[o + 2 * n] + lin[o + 2 * n + 2];
     }
     __syncthreads();
-    adi_iterations<true, S_SMEM ? 2 : 8, TW>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
+    adi_iterations<true, S_SMEM ? 2 : 8, TW, OTW>(gp, sh, a, it, S, Fa, ld, c, 0, total_it, timed_out);
     // T1 = Lambda C02 on nsl * Nzfull columns: T1[a][b'] = sum_t Lambda[a][b' - t] C02[b' - t][t]
     for (int e = tid; e < M * Wf; e += nth) {
       const int aa = e / Wf, cc = e - aa * Wf;
@@ -1393,13 +1401,13 @@ cudaError_t launch_sum_partials(const double *part, int n, double scale, double 
   return cudaGetLastError();
 }
 
-template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW, bool OTW = false>
 static cudaError_t launch_adjoint_t(const AdiArgs &a, const AdjointArgs &g, int threads, size_t smem,
                                     cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW>,
+  cudaError_t e = cudaFuncSetAttribute(adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW, OTW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW><<<a.nitems, threads, smem, st>>>(a, g);
+  adi_adjoint_kernel<S_SMEM, F_SMEM, MAXT, TW, OTW><<<a.nitems, threads, smem, st>>>(a, g);
   return cudaGetLastError();
 }
 
@@ -1409,6 +1417,9 @@ static cudaError_t launch_adjoint_level(const AdiArgs &a, const AdjointArgs &g, 
   if (a.twist_half > 0) {   // twisted records: 2 x 128 threads, or 2 x 256 with Fa in global memory
     if (threads <= 128) return launch_adjoint_t<S_SMEM, F_SMEM, 128, true>(a, g, threads, smem, st);
     if (threads <= 256) return launch_adjoint_t<S_SMEM, F_SMEM, 256, true>(a, g, threads, smem, st);
+    if constexpr (!S_SMEM && !F_SMEM) {
+      if (a.all_twisted) return launch_adjoint_t<false, false, 512, true, true>(a, g, threads, smem, st);
+    }
     if constexpr (!F_SMEM) return launch_adjoint_t<S_SMEM, false, 512, true>(a, g, threads, smem, st);
     else return cudaErrorInvalidValue;
   }
@@ -1426,12 +1437,12 @@ cudaError_t launch_adjoint(const AdiArgs &a, const AdjointArgs &g, int threads, 
   return launch_adjoint_level<false, false>(a, g, threads, smem, st);
 }
 
-template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW>
+template <bool S_SMEM, bool F_SMEM, int MAXT, bool TW, bool OTW = false>
 static cudaError_t launch_adi_t(const AdiArgs &a, int threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(adi_kernel<S_SMEM, F_SMEM, MAXT, TW>,
+  cudaError_t e = cudaFuncSetAttribute(adi_kernel<S_SMEM, F_SMEM, MAXT, TW, OTW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adi_kernel<S_SMEM, F_SMEM, MAXT, TW><<<a.nitems, threads, smem, st>>>(a);
+  adi_kernel<S_SMEM, F_SMEM, MAXT, TW, OTW><<<a.nitems, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1440,6 +1451,9 @@ static cudaError_t launch_adi_level(const AdiArgs &a, int threads, size_t smem, 
   if (a.twist_half > 0) {   // twisted plans: 2 x 128 threads, or 2 x 256 with Fa in global memory
     if (threads <= 128) return launch_adi_t<S_SMEM, F_SMEM, 128, true>(a, threads, smem, st);
     if (threads <= 256) return launch_adi_t<S_SMEM, F_SMEM, 256, true>(a, threads, smem, st);
+    if constexpr (!S_SMEM && !F_SMEM) {
+      if (a.all_twisted) return launch_adi_t<false, false, 512, true, true>(a, threads, smem, st);
+    }
     if constexpr (!F_SMEM) return launch_adi_t<S_SMEM, false, 512, true>(a, threads, smem, st);
     else return cudaErrorInvalidValue;
   }

@@ -47,6 +47,7 @@ struct AdiArgs {
   const double *corr;      // right-side correction of the lifted problem (class positions), or NULL
   int test_no_tma;         // failure-detection test: never start table copies, so waits run out
   int cluster;             // > 1: CTAs of a thread-block cluster per item (work arrays in global memory)
+  int all_twisted;         // every item's records (of the system this launch solves) twisted both ways
 };
 
 constexpr int CYL_ERR_TIMEOUT = 4;

@@ -288,9 +288,10 @@ class Plan:
 
     def launch_info(self, which):
         """Launch layout of one kind's ADI kernel (see include/cyl.h: cyl_plan_launch_info)."""
-        info = (ctypes.c_int * 8)()
+        info = (ctypes.c_int * 9)()
         _check(_lib.cyl_plan_launch_info(self._h, which, info), 'cyl_plan_launch_info')
-        keys = ('items', 'threads', 'twist_half', 'placement', 'smem', 'ctas_per_item', 'slices', 'built')
+        keys = ('items', 'threads', 'twist_half', 'placement', 'smem', 'ctas_per_item', 'slices', 'built',
+                'all_twisted')
         return dict(zip(keys, list(info)))
 
     def item_tables(self, which, item, j, transposed=False):

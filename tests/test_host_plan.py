@@ -321,7 +321,7 @@ def test_cluster_plans_twist_every_item(cyl):
     ((256, 256, 256), 0, (1, 128, 256, 1)),          # a single slice's iterate fits shared memory
     ((128, 128, 128), 0, (2, 128, 256, 2)),          # two-slice items in shared memory, twisted
     ((128, 128, 128), 'plain', (2, 0, 128, 2)),
-    ((20, 19, 8), 'global', (1, 32, 64, 0)),
+    ((20, 19, 8), 'global', (1, 32, 64, 0)),         # radial class 9: one-sided radial, not all twisted
     ((8, 520, 4), 0, (2, 0, 512, 1)),                # 518 radial chains on 512 threads
     ((600, 600, 8), 0, (2, 0, 512, 0)),              # class sizes above 256: one-sided, threads loop
 ])
@@ -333,6 +333,8 @@ def test_launch_layouts(cyl, mnp, flags, want):
     li = plan.launch_info(1)
     assert (li['slices'], li['twist_half'], li['threads'], li['placement']) == want, li
     assert li['built'] == 1 and li['ctas_per_item'] == 1 and li['smem'] <= 226 * 1024
+    # single-slice twisted layouts of large grids: every item twisted both ways
+    assert li['all_twisted'] == (1 if (want[0] == 1 and want[1] >= 128) else li['all_twisted'])
     m, n, p = mnp
     h = p // 2
     pairs = h - 1
