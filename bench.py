@@ -350,7 +350,7 @@ class Workload:
 class Heat128(Workload):
     name = 'heat128'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 100-step adi_kernel launch of the bench
-    TRAFFIC = (49316608 + 977664, '520e070b9b49')
+    TRAFFIC = (49248768 + 955648, 'ffba7142cab2')
     TRAFFIC_BASIS = 'ncu capture of the bench launch'
 
     def __init__(self, cyl, torch, dev, stream, nsteps):
@@ -473,9 +473,9 @@ class Poisson33(Workload):
 class Large512(Workload):
     name = 'large512'
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two adi_kernel launches on the same
-    # workload with n_theta = 320 (Poisson 34,195,699,200 + 35,829,435,648; 20 heat steps
-    # 576,059,499,520 + 558,830,722,304), scaled to n_theta = 512 by the items processed
-    TRAFFIC = (34195699200 + 35829435648 + 576059499520 + 558830722304, '520e070b9b49')
+    # workload with n_theta = 320 (Poisson 34,363,588,864 + 36,120,797,184; 20 heat steps
+    # 578,702,761,728 + 567,079,933,440), scaled to n_theta = 512 by the items processed
+    TRAFFIC = (34363588864 + 36120797184 + 578702761728 + 567079933440, 'ffba7142cab2')
     TRAFFIC_BASIS = 'ncu capture of the step at n_theta = 320 (two launches), scaled by 512 / 320'
     TRAFFIC_NTHETA = 320
 
