@@ -345,9 +345,9 @@ __global__ void __launch_bounds__(256, 6) chirp_xform_kernel(const double *in, d
   const long long nlines = outer * inner;
   const long long nfft = (nlines + LPF - 1) / LPF;
   const int Pm = P - 1;
-  __shared__ long long lbase[2 * kMaxXformFfts];     // first element of each line of this round, or -1
+  __shared__ long long lbase[2 * kMaxXformFfts];     // first element of each line of this FFT group, or -1
   for (long long f0 = (long long)blockIdx.x * G; f0 < nfft; f0 += (long long)gridDim.x * G) {
-    const int Gc = (int)min((long long)G, nfft - f0);     // FFTs in this round
+    const int Gc = (int)min((long long)G, nfft - f0);     // FFTs in this group
     const long long q0 = f0 * LPF;
     const int nl = (int)min((long long)Gc * LPF, nlines - q0);
     for (int e = threadIdx.x; e < Gc * LPF; e += blockDim.x) {
