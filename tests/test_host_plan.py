@@ -307,6 +307,8 @@ def test_cluster_plans_twist_every_item(cyl):
     plain.close()
     plan = cyl.Plan(m, n, p, 0.6, 2e-3, 1e-13, poisson=True, heat=True, host_only=True,
                     extra_flags=cyl.FORCE_CLUSTER)
+    li = plan.launch_info(1)
+    assert li['ctas_per_item'] > 1 and li['all_twisted'] == 0          # cluster launches keep their own kernel
     rng = np.random.default_rng(17)
     for which, item in ((0, 0), (1, 3)):
         kr, kz = _drive_item_to_direct_solve(cyl, plan, which, item, rng)
